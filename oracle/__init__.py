@@ -1,0 +1,255 @@
+"""FP64 CPU oracle for the Oblique-MERF hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never does, and
+this package imports nothing from it.
+
+Functions follow Oblique-MERF (arXiv 2404.09531):
+  render / features / occupancy_value / mlp / view_encoding   Eqs. 1-4, 6-8, appendix A
+  train (loss + analytic gradient)                             Eqs. 5, 9-10, 12
+  camera_rays                                                  pinhole rays (FP32 rule)
+  brick_table                                                  Sec. 4.4 brick allocation
+
+Parity status: every function is pinned in tests/test_oracle.py by closed
+forms, invariants, library routines or brute force (see that file).  No
+function is pinned to a value the paper prints: the paper prints no worked
+example for any synthetic input.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "omerf_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+NPARAM = 883
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the system C compiler (OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["cc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+               "-o", _LIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class _Scene(ctypes.Structure):
+    _fields_ = [
+        ("aabb", ctypes.c_float * 6),
+        ("L", ctypes.c_int32 * 3),
+        ("brick", ctypes.c_int32),
+        ("table", ctypes.c_void_p),
+        ("grid", ctypes.c_void_p),
+        ("R", ctypes.c_int32 * 3),
+        ("pxy", ctypes.c_void_p),
+        ("pxz", ctypes.c_void_p),
+        ("pyz", ctypes.c_void_p),
+        ("M", ctypes.c_int32),
+        ("occ", ctypes.c_void_p),
+        ("mlp", ctypes.c_void_p),
+        ("step", ctypes.c_float),
+        ("eps", ctypes.c_float),
+        ("t_thr", ctypes.c_float),
+        ("bg", ctypes.c_float * 3),
+        ("n_max", ctypes.c_int32),
+    ]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        lib.or_render.restype = ctypes.c_long
+        lib.or_render.argtypes = [P, P, ctypes.c_long, P, P, P, P, P, P, P, ctypes.c_int]
+        lib.or_train.restype = ctypes.c_int
+        lib.or_train.argtypes = [P, P, P, P, ctypes.c_long, ctypes.c_int, P, ctypes.c_double, P,
+                                 P, P, P, P, P, P, P]
+        lib.or_features.restype = ctypes.c_long
+        lib.or_features.argtypes = [P, P, ctypes.c_long, P]
+        lib.or_occupancy_value.restype = ctypes.c_double
+        lib.or_occupancy_value.argtypes = [ctypes.c_double] * 4
+        lib.or_view_encoding.restype = None
+        lib.or_view_encoding.argtypes = [P, P]
+        lib.or_mlp.restype = None
+        lib.or_mlp.argtypes = [P, P, P, ctypes.c_long, P]
+        lib.or_camera_rays.restype = None
+        lib.or_camera_rays.argtypes = [P, ctypes.c_int, ctypes.c_int, P]
+        lib.or_brick_table.restype = ctypes.c_long
+        lib.or_brick_table.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int, P]
+        lib.or_ray_weights.restype = ctypes.c_int
+        lib.or_ray_weights.argtypes = [P, P, P, P]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+class OracleScene:
+    """FP64 copies of a scene's arrays plus the C descriptor that points at them.
+
+    ``scene`` is a dict as produced by ``synth.make_scene`` (keys grid, table,
+    p_xy, p_xz, p_yz, occ, mlp, spec); values are widened to float64 exactly.
+    Keyword overrides replace scalar settings (step, eps, t_thr, n_max, bg).
+    """
+
+    def __init__(self, scene: dict, **over):
+        spec = scene["spec"]
+        self.spec = spec
+        self.grid = _f64(scene["grid"])
+        self.table = None if scene.get("table") is None else np.ascontiguousarray(scene["table"], np.int32)
+        self.pxy = _f64(scene["p_xy"])
+        self.pxz = _f64(scene["p_xz"])
+        self.pyz = _f64(scene["p_yz"])
+        self.occ = _f64(scene["occ"])
+        self.mlp = _f64(scene["mlp"])
+        self.step = np.float32(over.get("step", spec.step))
+        self.eps = np.float32(over.get("eps", spec.eps))
+        self.t_thr = np.float32(over.get("t_thr", spec.t_thr))
+        self.n_max = int(over.get("n_max", spec.n_max))
+        self.bg = np.asarray(over.get("bg", (0.0, 0.0, 0.0)), np.float32)
+        self.brick = int(spec.brick if self.table is not None else 0)
+
+    def desc(self) -> _Scene:
+        s = _Scene()
+        spec = self.spec
+        s.aabb[:] = [float(np.float32(v)) for v in spec.aabb]
+        s.L[:] = list(spec.L)
+        s.brick = self.brick
+        s.table = _ptr(self.table)
+        s.grid = _ptr(self.grid)
+        s.R[:] = list(spec.R)
+        s.pxy, s.pxz, s.pyz = _ptr(self.pxy), _ptr(self.pxz), _ptr(self.pyz)
+        s.M = spec.M
+        s.occ = _ptr(self.occ)
+        s.mlp = _ptr(self.mlp)
+        s.step = float(self.step)
+        s.eps = float(self.eps)
+        s.t_thr = float(self.t_thr)
+        s.bg[:] = [float(v) for v in self.bg]
+        s.n_max = self.n_max
+        return s
+
+
+def render(oscene: OracleScene, rays: np.ndarray, nthreads: int = 0) -> dict:
+    """Forward render (Eqs. 1-4, 6-8) of rays [n][6] float32."""
+    lib = _load()
+    rays = np.ascontiguousarray(rays, np.float32)
+    n = rays.shape[0]
+    out = {
+        "rgb": np.zeros((n, 3)), "count": np.zeros(n, np.int32), "F": np.zeros((n, 7)),
+        "TN": np.zeros(n), "ambiguous": np.zeros(n, np.int32),
+        "k_first": np.zeros(n, np.int32), "k_last": np.zeros(n, np.int32),
+    }
+    d = oscene.desc()
+    ua = lib.or_render(ctypes.byref(d), _ptr(rays), n, _ptr(out["rgb"]), _ptr(out["count"]),
+                       _ptr(out["F"]), _ptr(out["TN"]), _ptr(out["ambiguous"]),
+                       _ptr(out["k_first"]), _ptr(out["k_last"]), int(nthreads))
+    out["unalloc"] = int(ua)
+    return out
+
+
+def ray_weights(oscene: OracleScene, ray: np.ndarray):
+    lib = _load()
+    ray = np.ascontiguousarray(ray, np.float32).reshape(6)
+    w = np.zeros(max(oscene.n_max, 1))
+    tn = np.zeros(1)
+    d = oscene.desc()
+    cnt = lib.or_ray_weights(ctypes.byref(d), _ptr(ray), _ptr(w), _ptr(tn))
+    return w[:cnt], float(tn[0])
+
+
+def train(oscene: OracleScene, rays, target, smooth_dirs, lam=(1.0, 1e-2, 0.0), grad_scale=1.0,
+          want_grad=True) -> dict:
+    """Loss (Eqs. 5, 10, 12) and its FP64 gradient w.r.t. every parameter."""
+    lib = _load()
+    rays = np.ascontiguousarray(rays, np.float32)
+    target = np.ascontiguousarray(target, np.float32)
+    smooth_dirs = np.ascontiguousarray(smooth_dirs, np.float32)
+    n = rays.shape[0]
+    K = smooth_dirs.shape[1] if smooth_dirs.ndim == 3 else 1
+    if K > 16:
+        raise ValueError("the oracle supports at most 16 smoothness directions per ray")
+    lam = np.asarray(lam, np.float64)
+    loss = np.zeros(4)
+    sig = np.zeros(1, np.uint64)
+    g = {}
+    if want_grad:
+        g = {"grid": np.zeros_like(oscene.grid), "p_xy": np.zeros_like(oscene.pxy),
+             "p_xz": np.zeros_like(oscene.pxz), "p_yz": np.zeros_like(oscene.pyz),
+             "occ": np.zeros_like(oscene.occ), "mlp": np.zeros_like(oscene.mlp)}
+    d = oscene.desc()
+    rc = lib.or_train(ctypes.byref(d), _ptr(rays), _ptr(target), _ptr(smooth_dirs), n, K, _ptr(lam),
+                      float(grad_scale), _ptr(loss), _ptr(g.get("grid")), _ptr(g.get("p_xy")),
+                      _ptr(g.get("p_xz")), _ptr(g.get("p_yz")), _ptr(g.get("occ")), _ptr(g.get("mlp")),
+                      _ptr(sig))
+    if rc != 0:
+        raise MemoryError("oracle train failed")
+    return {"loss": float(loss[0]), "loss_terms": loss[1:].copy(), "grads": g, "signature": int(sig[0])}
+
+
+def features(oscene: OracleScene, pts: np.ndarray):
+    lib = _load()
+    pts = np.ascontiguousarray(pts, np.float64)
+    out = np.zeros((pts.shape[0], 8))
+    d = oscene.desc()
+    ua = lib.or_features(ctypes.byref(d), _ptr(pts), pts.shape[0], _ptr(out))
+    return out, int(ua)
+
+
+def occupancy_value(z, zmin, zmax, eps) -> float:
+    return float(_load().or_occupancy_value(float(z), float(zmin), float(zmax), float(eps)))
+
+
+def view_encoding(direction) -> np.ndarray:
+    d = np.ascontiguousarray(direction, np.float64).reshape(3)
+    enc = np.zeros(27)
+    _load().or_view_encoding(_ptr(d), _ptr(enc))
+    return enc
+
+
+def mlp(params, F, dirs) -> np.ndarray:
+    params = _f64(params)
+    F = _f64(np.atleast_2d(F))
+    dirs = _f64(np.atleast_2d(dirs))
+    out = np.zeros((F.shape[0], 3))
+    _load().or_mlp(_ptr(params), _ptr(F), _ptr(dirs), F.shape[0], _ptr(out))
+    return out
+
+
+def camera_rays(cam: dict) -> np.ndarray:
+    """Pixel-centre pinhole rays [H*W][6] float32 (row-major pixels)."""
+    c = np.zeros(16, np.float32)
+    c[:12] = np.asarray(cam["c2w"], np.float32).reshape(12)
+    c[12:] = [cam["fx"], cam["fy"], cam["cx"], cam["cy"]]
+    W, H = int(cam["width"]), int(cam["height"])
+    rays = np.zeros((H * W, 6), np.float32)
+    _load().or_camera_rays(_ptr(c), W, H, _ptr(rays))
+    return rays
+
+
+def brick_table(spec, occ: np.ndarray) -> np.ndarray:
+    """Sec. 4.4 brick allocation -> int32 table [nbx][nby][nbz] (-1 = empty)."""
+    B = spec.brick
+    nb = [(l + B - 1) // B for l in spec.L]
+    table = np.zeros(nb, np.int32)
+    aabb = np.asarray(spec.aabb, np.float32)
+    L = np.asarray(spec.L, np.int32)
+    occ = np.ascontiguousarray(occ, np.float32)
+    _load().or_brick_table(_ptr(aabb), _ptr(L), B, _ptr(occ), spec.M, _ptr(table))
+    return table
