@@ -1,0 +1,353 @@
+"""Benchmark of the Oblique-MERF hot path on GB300.
+
+Default workload (one step): forward render of 8 oblique 1920x1080 cameras over
+the sparse 512x512x32 city scene with 2048^2 / 2048x128 planes (FP32 features),
+i.e. 16.6 M rays per step.  The same JSON line also reports one training step
+(forward + backward, 2^18 rays on the 64x64x16 heightfield scene).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Timing: W untimed warm-up steps, then K timed steps; each camera render is
+bracketed by CUDA events on the stream the kernels run on, and L2 is flushed
+(a 256 MiB write) between steps outside the timed events.  Under torchrun each
+rank renders its own cameras (weak scaling, no data exchange); rank 0 prints
+one JSON line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+BYTES_PER_SAMPLE = {"f32": 640 + 8, "bf16": 320 + 8}  # feature gather + occupancy bounds
+BYTES_PER_RAY_RENDER = 12 + 4                          # rgb + count written
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
+# from the ncu capture summarised in profiles/ (None until captured for the
+# current kernel version).
+TRAFFIC_PER_LAUNCH = None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.proc = None
+        self.path = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "0x1") or v == "1":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload_config():
+    spec = synth.scene_spec(2)
+    return {"workload": "render 8 oblique cameras 1920x1080, sparse 512x512x32 grid (8^3 bricks, "
+                        "15% allocated), planes 2048^2 / 2048x128, occupancy 256^2, step 1/2048, "
+                        "n_max 512, FP32 features",
+            "rays_per_step": spec.n_cams * spec.width * spec.height,
+            "l2": "flushed between steps (256 MiB write)",
+            "train_workload": "fwd+bwd 2^18 rays, 64x64x16 grid, 256^2/256x32 planes, occupancy 32^2, "
+                              "step 1/256, K=1 smoothness direction, FP32"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores (bounded sample)
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle  # the oracle is this build's reference program
+
+    sc = synth.make_scene(2)
+    table = oracle.brick_table(sc["spec"], sc["occ"])
+    pool = synth.fill_brick_pool(sc, table)
+    osc = oracle.OracleScene(dict(sc, grid=pool, table=table))
+    cams = synth.make_cameras(2)
+    rays = np.concatenate([oracle.camera_rays(c) for c in cams])
+    cores = os.cpu_count() or 1
+    sample = rays[:: max(1, rays.shape[0] // 32768)]
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.render(osc, sample, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    t = float(np.mean(times))
+    value = sample.shape[0] / t / 1e6
+    cfg = _workload_config()
+    line = {"metric": "Mrays/s render & fwd+bwd train, BF16 vs FP32 at matched PSNR vs FP64 oracle",
+            "impl": "reference", "value": value, "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample.shape[0]} rays, every {rays.shape[0] // sample.shape[0]}th "
+                                       f"ray of the 8 cameras"},
+            "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(sc, cams, budget_s=12.0):
+    """The oracle, as it stands, on a bounded sample of the same workload."""
+    import oracle
+
+    table = oracle.brick_table(sc["spec"], sc["occ"])
+    pool = synth.fill_brick_pool(sc, table)
+    osc = oracle.OracleScene(dict(sc, grid=pool, table=table))
+    rays = np.concatenate([oracle.camera_rays(c) for c in cams])
+    cores = os.cpu_count() or 1
+    probe = rays[:: max(1, rays.shape[0] // 4096)]
+    t0 = time.perf_counter()
+    oracle.render(osc, probe, nthreads=cores)
+    per_ray = (time.perf_counter() - t0) / probe.shape[0]
+    n = int(min(rays.shape[0], max(4096, budget_s / max(per_ray, 1e-9))))
+    stride = max(1, rays.shape[0] // n)
+    sample = rays[::stride]
+    t0 = time.perf_counter()
+    oracle.render(osc, sample, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample.shape[0] / dt / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sample.shape[0]} rays (every {stride}th ray of the 8 cameras), {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def run_native(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_2404_09531_gb300 as om
+
+    # ---- scene (config 2) ----
+    sc = synth.make_scene(2)
+    spec = sc["spec"]
+    occ = torch.as_tensor(sc["occ"]).to(dev)
+    table_t, _ = om.build_brick_table(spec.aabb, spec.L, spec.brick, occ)
+    table = table_t.cpu().numpy()
+    scene = om.scene_from_synth(sc, device=dev, table=table)
+    cams = synth.make_cameras(2)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        outs = []
+        for i, cam in enumerate(cams):
+            if events is not None:
+                events[i][0].record(stream)
+            outs.append(om.render(scene, camera=cam, want_count=False))
+            if events is not None:
+                events[i][1].record(stream)
+        return outs
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    rgb0, cnt0 = om.render(scene, camera=cams[0])
+    samples_per_step = 0
+    for cam in cams:
+        _, c = om.render(scene, camera=cam)
+        samples_per_step += int(c.sum().item())
+    rays_per_step = sum(c["width"] * c["height"] for c in cams)
+
+    clocks = ClockSampler(None)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    per_launch = []
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in cams]
+        step(ev)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        per_launch += ms
+        step_ms.append(sum(ms))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_step = float(np.mean(step_ms))
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+        dist.barrier()
+    value = ws * rays_per_step / (t_step * 1e-3) / 1e6
+
+    # ---- end to end through the public API, host buffers ----
+    host_rgb = [torch.empty((c["width"] * c["height"], 3), dtype=torch.float32, pin_memory=True) for c in cams]
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for cam, h in zip(cams, host_rgb):
+            om.render(scene, camera=cam, out=h, want_count=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_step = float(np.mean(e2e_ms))
+    d2h = sum(h.numel() * 4 for h in host_rgb)
+    h2d = 64 * len(cams)  # camera structs (the step's only input)
+
+    # ---- training step (config 3) ----
+    tsc = synth.make_scene(3)
+    tscene = om.scene_from_synth(tsc, device=dev)
+    batch = synth.make_train_batch(3, 1 << 18)
+    target, _ = om.render(om.scene_from_synth(synth.perturb_scene(tsc), device=dev), rays=batch["rays"])
+    rays_d = torch.as_tensor(batch["rays"]).to(dev)
+    dirs_d = torch.as_tensor(batch["smooth_dirs"]).to(dev)
+    grads = om.binding._zero_grads(tscene)
+    saved = torch.empty((1 << 18) * om.saved_bytes_per_ray() // 4, dtype=torch.float32, device=dev)
+    lam = (1.0, 1e-2, 1e-4)
+    for _ in range(args.warmup):
+        om.train_step(tscene, rays_d, target, dirs_d, lam=lam, grads=grads, saved=saved)
+    tr_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        for g in grads.values():
+            g.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = om.train_step(tscene, rays_d, target, dirs_d, lam=lam, grads=grads, saved=saved)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tr_ms.append(a.elapsed_time(b))
+    t_train = float(np.mean(tr_ms))
+    loss = res["loss"].cpu().numpy().tolist()
+
+    if rank != 0:
+        return 0
+
+    hbm, peak_kind = _peaks()
+    t_launch = float(np.mean(per_launch)) * 1e-3
+    bytes_launch = (samples_per_step * BYTES_PER_SAMPLE["f32"] + rays_per_step * BYTES_PER_RAY_RENDER) / len(cams)
+    achieved = bytes_launch / t_launch / 1e9
+    cfg = _workload_config()
+    cfg["samples_per_step"] = samples_per_step
+    cfg["mean_samples_per_ray"] = samples_per_step / rays_per_step
+    line = {
+        "metric": "Mrays/s render & fwd+bwd train, BF16 vs FP32 at matched PSNR vs FP64 oracle",
+        "value": value, "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded oblique city scene; paper datasets unavailable)",
+        "config": cfg,
+        "msamples_per_s": ws * samples_per_step / (t_step * 1e-3) / 1e6,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": TRAFFIC_PER_LAUNCH,
+                     "kernel": "march_fwd_kernel<float, sparse, render>",
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                     "algorithmic_bytes_per_launch": bytes_launch},
+        "e2e": {"value": ws * rays_per_step / (e2e_step * 1e-3) / 1e6, "unit": "Mrays/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
+        "train": {"metric": "Mrays/s fwd+bwd train", "value": (1 << 18) / (t_train * 1e-3) / 1e6,
+                  "unit": "Mrays/s", "ms_per_step": t_train, "rays_per_step": 1 << 18, "loss": loss},
+        "gpu_launches": args.steps * len(cams),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(sc, cams)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * omerf.h -- C ABI of the GB300 (sm_103a) Oblique-MERF hot path.
+ *
+ * Oblique-MERF (arXiv 2404.09531) renders a ray by marching through a
+ * low-resolution feature grid plus three high-resolution feature planes
+ * (Sec. 3, Eq. 2), restricted to the interval [z_min, z_max] that an
+ * occupancy plane stores for the nearest (x, y) grid point (Sec. 4.1,
+ * Eqs. 6-8), alpha-compositing diffuse colour and specular features front to
+ * back (Eq. 1) and shading the pixel with a small deferred MLP (Eq. 4).
+ * Training adds a photometric Charbonnier loss (Eq. 12), a view-direction
+ * smoothness loss (Eqs. 9-10) and an interval-span loss (Eq. 5).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named "device" point to CUDA device memory owned by the caller
+ *     (for example PyTorch tensors); the library never frees them and never
+ *     keeps them beyond the scene handle's lifetime.  "host" pointers are
+ *     read before the call returns.
+ *   - Layouts are channel-last and x-major:
+ *       dense grid   [Lx][Ly][Lz][8]
+ *       brick pool   [n_bricks][B][B][B][8] with brick table [nbx][nby][nbz]
+ *                    (nb? = ceil(L?/B), entries are pool indices or -1)
+ *       planes       XY [Rx][Ry][8], XZ [Rx][Rz][8], YZ [Ry][Rz][8]
+ *       occupancy    [M][M][2] = (z_min, z_max), cell (i, j) covers
+ *                    x0 + [i, i+1) (x1-x0)/M by y0 + [j, j+1) (y1-y0)/M
+ *       MLP          883 floats: W1[16][34] b1[16] W2[16][16] b2[16] W3[3][16] b3[3]
+ *                    input = [F (7), d, sin(2^k d), cos(2^k d) for k = 0..3]
+ *       rays         [n][6] = (origin, unit direction), float32
+ *   - Features are float32 (OMERF_F32) or bfloat16 (OMERF_BF16); every
+ *     accumulation, the transmittance and the sample schedule are float32.
+ *   - Which lattice samples t_k = k * step (k >= 0) a ray evaluates is
+ *     decided in float32 without fused multiply-add: p = o + t_k d, p inside
+ *     the box (closed), nearest occupancy cell c = floor((x - x0) * (M /
+ *     (x1 - x0))) clamped to [0, M-1] (same for y), z_min(c) < z < z_max(c).
+ *     A ray stops after the sample where its transmittance drops below t_thr
+ *     (0 disables), or after n_max evaluated samples, and uses lattice
+ *     indices k < 2^24 only.
+ *   - Every call is asynchronous on the given CUDA stream (NULL = the legacy
+ *     default stream).  Errors found on the host (bad sizes, null pointers,
+ *     misaligned pointers) return a negative status before anything is
+ *     launched; CUDA launch errors return OMERF_ECUDA; errors raised while a
+ *     kernel runs surface at the next call or at omerf_sync.
+ *   - omerf_last_error() returns a thread-local message for the last failure.
+ *   - Calls that share one scene handle must be ordered on one stream: a
+ *     render or training launch uses the scene's internal work counters.
+ */
+#ifndef OMERF_H
+#define OMERF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OMERF_OK = 0,
+    OMERF_EINVAL = -1,   /* invalid argument (null pointer, bad enum, bad value) */
+    OMERF_ESHAPE = -2,   /* inconsistent sizes */
+    OMERF_EDEVICE = -3,  /* no usable CUDA device, or a pointer is not device memory */
+    OMERF_ECUDA = -4,    /* a CUDA runtime call failed */
+    OMERF_ETIMEOUT = -5, /* omerf_sync gave up waiting */
+    OMERF_ENOMEM = -6    /* the library could not allocate its own state */
+} omerf_status;
+
+enum { OMERF_F32 = 0, OMERF_BF16 = 1 };
+
+/* Scene description.  All array pointers are device pointers owned by the
+ * caller and must stay valid while the scene handle exists. */
+typedef struct {
+    float aabb[6];             /* x0, x1, y0, y1, z0, z1 (x1 > x0 etc.) */
+    int32_t grid_res[3];       /* grid vertices Lx, Ly, Lz (each >= 2) */
+    int32_t brick;             /* brick edge B in vertices (power of two, 2..32), 0 = dense grid */
+    int32_t n_bricks;          /* number of pool bricks (brick grids only) */
+    int32_t plane_res[3];      /* plane texels Rx, Ry, Rz (each >= 2) */
+    int32_t occ_res;           /* occupancy cells per axis M (>= 1) */
+    int32_t feat_dtype;        /* OMERF_F32 or OMERF_BF16 (grid and planes) */
+    float step;                /* lattice spacing; must be a power of two */
+    float eps_occ;             /* ramp width epsilon of Eq. 6 (> 0); q = 2 */
+    float t_thr;               /* early-termination threshold on T (>= 0) */
+    float bg[3];               /* background colour added as T_N * bg */
+    int32_t n_max;             /* maximum evaluated samples per ray (1..65536) */
+    const void *grid;          /* device: dense grid or brick pool, 16-byte aligned */
+    const int32_t *brick_table;/* device: brick table (brick grids only) */
+    const void *plane_xy;      /* device, 16-byte aligned */
+    const void *plane_xz;      /* device, 16-byte aligned */
+    const void *plane_yz;      /* device, 16-byte aligned */
+    const float *occ;          /* device: [M][M][2], 8-byte aligned */
+    const float *mlp;          /* device: 883 float32 weights (always float32) */
+} omerf_scene_desc;
+
+/* Pinhole camera.  c2w is the 3x4 row-major camera-to-world matrix [R | o];
+ * the camera looks down its -z axis, image rows go along -y.  The ray of
+ * pixel (px, py) has direction normalize(R (u, v, -1)) with
+ * u = (px + 0.5 - cx) / fx and v = -(py + 0.5 - cy) / fy, evaluated in
+ * float32 left to right without fused operations; ray index py * width + px. */
+typedef struct {
+    float c2w[12];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} omerf_camera;
+
+typedef struct omerf_scene omerf_scene;
+
+/* Create a scene handle from a description (validated on the host).  The
+ * handle owns small device state only: the occupancy hull used to bound each
+ * ray and per-launch work counters.  It builds that state on `stream` and
+ * returns without synchronising.  Errors: OMERF_EINVAL / OMERF_ESHAPE for bad
+ * descriptions, OMERF_ENOMEM / OMERF_ECUDA if its state cannot be allocated. */
+omerf_status omerf_scene_create(const omerf_scene_desc *desc, void *stream, omerf_scene **out);
+
+/* Recompute the scene's occupancy hull after the caller changed occ in
+ * place (for example after an optimiser step on z_min / z_max). */
+omerf_status omerf_scene_update(omerf_scene *scene, void *stream);
+
+/* Free the handle's own device state (not the caller's arrays). */
+void omerf_scene_destroy(omerf_scene *scene);
+
+/* Occupancy-driven brick allocation (Sec. 4.4: features are stored only
+ * where the occupancy plane marks space as occupied).  Brick (bi, bj, bk)
+ * of B^3 vertices is allocated iff an occupancy cell overlapping the brick's
+ * xy footprint dilated by one voxel has a non-empty [z_min, z_max] meeting
+ * the brick's z-range dilated by one voxel (float32 test).  Pool indices
+ * are assigned in x-major brick order.
+ *   occ      device [M][M][2]
+ *   table    device int32 [ceil(Lx/B)][ceil(Ly/B)][ceil(Lz/B)] (output)
+ *   n_alloc  device int32 scalar (output): number of allocated bricks
+ * The dilation guarantees that no evaluated sample interpolates a vertex of
+ * an unallocated brick. */
+omerf_status omerf_build_brick_table(const float aabb[6], const int32_t grid_res[3], int32_t brick,
+                                     const float *occ, int32_t occ_res, int32_t *table,
+                                     int32_t *n_alloc, void *stream);
+
+/* Ray interval (box and occupancy-slab intersection, Sec. 4.4's bounding-box
+ * skipping): for each ray, the inclusive lattice index range [k_lo, k_hi]
+ * that the march scans.  Every evaluated sample of the ray lies inside it;
+ * an empty range has k_lo > k_hi.
+ *   cam    host camera (then n must be width * height and rays NULL), or NULL
+ *   rays   device [n][6] when cam is NULL
+ *   k_range device int32 [n][2] (output) */
+omerf_status omerf_ray_interval(const omerf_scene *scene, const omerf_camera *cam, const float *rays,
+                                int64_t n, int32_t *k_range, void *stream);
+
+/* Forward render (Eqs. 1-4, 6-8): per ray, composite the evaluated samples
+ * and shade with the deferred MLP:
+ *     rgb = sum_i w_i c^d_i + G(F, d) + T_N * bg,  F = [sum w c^d, sum w f],
+ *     w_i = T_i M_i alpha_i,  T_{i+1} = T_i (1 - M_i alpha_i),
+ * and rgb = bg for a ray with no evaluated sample.
+ *   cam    host camera (n == width * height, rays NULL), or NULL
+ *   rays   device [n][6] float32 when cam is NULL
+ *   rgb    device float32 [n][3] (output)
+ *   count  device int32 [n] evaluated samples per ray (output, may be NULL)
+ * The deferred MLP runs in float32 for OMERF_F32 scenes and in bfloat16 on
+ * tensor cores with float32 accumulation for OMERF_BF16 scenes. */
+omerf_status omerf_render(const omerf_scene *scene, const omerf_camera *cam, const float *rays,
+                          int64_t n, float *rgb, int32_t *count, void *stream);
+
+/* Bytes of per-ray state that omerf_train_fwd writes for omerf_train_bwd. */
+int64_t omerf_saved_bytes_per_ray(void);
+
+/* Training forward (Eqs. 5, 9-10, 12), float32 features only:
+ *   L = lambda[0] * mean_r sqrt(|C_r - C*_r|^2 + 1e-6)
+ *     + lambda[1] * mean_r sum_k S(d, s_k) |G(F, s_k/|s_k|) - G(F, d)|^2
+ *     + lambda[2] * sum_cells (z_max - z_min)^2
+ * with S the cosine similarity and s_k = d + delta_k supplied by the caller.
+ *   rays        device [n][6]       target     device [n][3]
+ *   smooth_dirs device [n][K][3] (K in 0..16; may be NULL when K == 0)
+ *   lambda      host [3]
+ *   saved       device, n * omerf_saved_bytes_per_ray() bytes, 16-byte aligned (output)
+ *   loss        device float32 [4] (output): total, rgb, smooth, occ terms */
+omerf_status omerf_train_fwd(const omerf_scene *scene, const float *rays, const float *target,
+                             const float *smooth_dirs, int64_t n, int32_t K, const float lambda[3],
+                             void *saved, float *loss, void *stream);
+
+/* Training backward: recomputes each ray's march (no per-sample storage)
+ * and ACCUMULATES (+=) grad_scale * dL/dparam into caller-zeroed float32
+ * buffers shaped like the parameters (g_grid like the dense grid or the
+ * brick pool).  grad_scale is a device float32 scalar (NULL means 1).
+ * The same rays, target, smooth_dirs, K, lambda and saved state as the
+ * matching omerf_train_fwd call must be passed; the backward also writes the
+ * per-ray dL/dF and dL/dT_N into the second half of each saved record. */
+omerf_status omerf_train_bwd(const omerf_scene *scene, const float *rays, const float *target,
+                             const float *smooth_dirs, int64_t n, int32_t K, const float lambda[3],
+                             void *saved, const float *grad_scale, float *g_grid, float *g_xy,
+                             float *g_xz, float *g_yz, float *g_occ, float *g_mlp, void *stream);
+
+/* One fused training step: omerf_train_fwd then omerf_train_bwd with
+ * grad_scale 1 (loss written, gradients accumulated). */
+omerf_status omerf_train_step(const omerf_scene *scene, const float *rays, const float *target,
+                              const float *smooth_dirs, int64_t n, int32_t K, const float lambda[3],
+                              void *saved, float *loss, float *g_grid, float *g_xy, float *g_xz,
+                              float *g_yz, float *g_occ, float *g_mlp, void *stream);
+
+/* Wait for `stream` with a bounded host-side poll; returns OMERF_ETIMEOUT
+ * after timeout_ms milliseconds (< 0 waits without limit), OMERF_ECUDA if
+ * the stream reported an error. */
+omerf_status omerf_sync(void *stream, int32_t timeout_ms);
+
+/* Thread-local description of the last failure in this thread. */
+const char *omerf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OMERF_H */

@@ -242,6 +242,11 @@ static int slab_range(const or_scene *s, const float o[3], const float d[3], dou
         }
         double ta = (lo - o[a]) / d[a], tb = (hi - o[a]) / d[a];
         if (ta > tb) { double x = ta; ta = tb; tb = x; }
+        /* widen by far more than the FP32 error of the sample positions, so
+         * that the scan covers every lattice point the FP32 test accepts */
+        double pad = 1e-6 * (fmax(fabs(ta), fabs(tb)) + (fabs((double)o[a]) + 1.0) / fabs((double)d[a]));
+        ta -= pad;
+        tb += pad;
         if (ta > t0) t0 = ta;
         if (tb < t1) t1 = tb;
     }
@@ -283,9 +288,12 @@ static void march_ray(const or_scene *s, const float ray[6], or_sample *smp, or_
     const float *o = ray, *d = ray + 3;
     double tin, tout;
     if (!slab_range(s, o, d, &tin, &tout)) return;
-    long klo = (long)floor(tin / s->step) - 2;
-    long khi = (long)ceil(tout / s->step) + 2;
-    if (klo < 0) klo = 0;
+    /* lattice indices are limited to k < 2^24, where k * step is exact */
+    double fklo = floor(tin / s->step) - 2.0, fkhi = ceil(tout / s->step) + 2.0;
+    if (fklo < 0.0) fklo = 0.0;
+    if (fkhi > 16777215.0) fkhi = 16777215.0;
+    if (fklo > fkhi) return;
+    long klo = (long)fklo, khi = (long)fkhi;
     double T = 1.0;
     int n = 0;
     for (long k = klo; k <= khi; k++) {

@@ -1,0 +1,28 @@
+"""GB300 (sm_103a) Oblique-MERF hot path: Python binding of libomerf.so.
+
+Argument marshalling only: every step of the render and training paths runs
+in the CUDA kernels behind the C ABI declared in include/omerf.h.  PyTorch is
+used for device memory and streams.  There is no CPU fallback: if the shared
+library is missing or no GPU is present, calls raise.
+"""
+from .binding import (  # noqa: F401
+    OmerfError,
+    Scene,
+    TrainStep,
+    build_brick_table,
+    camera_struct,
+    lib,
+    ray_interval,
+    render,
+    saved_bytes_per_ray,
+    scene_from_synth,
+    sync,
+    train_bwd,
+    train_fwd,
+    train_step,
+)
+
+__all__ = [
+    "OmerfError", "Scene", "TrainStep", "build_brick_table", "camera_struct", "lib", "ray_interval", "render",
+    "saved_bytes_per_ray", "scene_from_synth", "sync", "train_bwd", "train_fwd", "train_step",
+]

@@ -1,0 +1,419 @@
+"""ctypes binding of the C ABI in include/omerf.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libomerf.so")
+_lib = None
+
+OMERF_F32 = 0
+OMERF_BF16 = 1
+MLP_NPARAM = 883
+
+
+class OmerfError(RuntimeError):
+    """A negative status returned by the library, with its message."""
+
+
+class _SceneDesc(ctypes.Structure):
+    _fields_ = [
+        ("aabb", ctypes.c_float * 6),
+        ("grid_res", ctypes.c_int32 * 3),
+        ("brick", ctypes.c_int32),
+        ("n_bricks", ctypes.c_int32),
+        ("plane_res", ctypes.c_int32 * 3),
+        ("occ_res", ctypes.c_int32),
+        ("feat_dtype", ctypes.c_int32),
+        ("step", ctypes.c_float),
+        ("eps_occ", ctypes.c_float),
+        ("t_thr", ctypes.c_float),
+        ("bg", ctypes.c_float * 3),
+        ("n_max", ctypes.c_int32),
+        ("grid", ctypes.c_void_p),
+        ("brick_table", ctypes.c_void_p),
+        ("plane_xy", ctypes.c_void_p),
+        ("plane_xz", ctypes.c_void_p),
+        ("plane_yz", ctypes.c_void_p),
+        ("occ", ctypes.c_void_p),
+        ("mlp", ctypes.c_void_p),
+    ]
+
+
+class _Camera(ctypes.Structure):
+    _fields_ = [
+        ("c2w", ctypes.c_float * 12),
+        ("fx", ctypes.c_float),
+        ("fy", ctypes.c_float),
+        ("cx", ctypes.c_float),
+        ("cy", ctypes.c_float),
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+    ]
+
+
+# name -> (restype, argtypes) for every entry point of include/omerf.h
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_L = ctypes.c_int64
+SIGNATURES = {
+    "omerf_scene_create": (ctypes.c_int, [_P, _P, _P]),
+    "omerf_scene_update": (ctypes.c_int, [_P, _P]),
+    "omerf_scene_destroy": (None, [_P]),
+    "omerf_build_brick_table": (ctypes.c_int, [_P, _P, _I, _P, _I, _P, _P, _P]),
+    "omerf_ray_interval": (ctypes.c_int, [_P, _P, _P, _L, _P, _P]),
+    "omerf_render": (ctypes.c_int, [_P, _P, _P, _L, _P, _P, _P]),
+    "omerf_saved_bytes_per_ray": (ctypes.c_int64, []),
+    "omerf_train_fwd": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P]),
+    "omerf_train_bwd": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "omerf_train_step": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "omerf_sync": (ctypes.c_int, [_P, _I]),
+    "omerf_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load libomerf.so from the package directory (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise OmerfError(f"{_LIB_PATH} is missing: build it with __graft_entry__.build()")
+        handle = ctypes.CDLL(_LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        msg = lib().omerf_last_error()
+        raise OmerfError(f"{what} failed with status {status}: {msg.decode() if msg else ''}")
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_f32(x, device, shape=None):
+    if x is None:
+        return None
+    t = torch.as_tensor(x)
+    t = t.to(device=device, dtype=torch.float32).contiguous()
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        t = t.reshape(shape)
+    return t
+
+
+def _require_cuda(t, name):
+    if not t.is_cuda:
+        raise OmerfError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise OmerfError(f"{name} must be contiguous")
+
+
+def camera_struct(cam) -> _Camera:
+    """A C camera from a dict with c2w (3x4), fx, fy, cx, cy, width, height."""
+    c = _Camera()
+    c.c2w[:] = [float(v) for v in np.asarray(cam["c2w"], np.float32).reshape(12)]
+    c.fx, c.fy, c.cx, c.cy = (float(np.float32(cam[k])) for k in ("fx", "fy", "cx", "cy"))
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    return c
+
+
+class Scene:
+    """A scene handle over caller-owned device tensors.
+
+    Tensors (channel-last, x-major; see include/omerf.h):
+      grid     dense [Lx, Ly, Lz, 8] or brick pool [nb, B, B, B, 8]
+      table    int32 brick table [nbx, nby, nbz] (brick grids) or None
+      p_xy, p_xz, p_yz   planes [Rx, Ry, 8], [Rx, Rz, 8], [Ry, Rz, 8]
+      occ      float32 [M, M, 2]      mlp float32 [883]
+    Features are float32 or bfloat16 (both grid and planes the same dtype).
+    The tensors are referenced, not copied: in-place updates are seen by the
+    next call (call update() after changing occ).
+    """
+
+    def __init__(self, *, aabb, grid, p_xy, p_xz, p_yz, occ, mlp, step, eps, t_thr=1e-4, n_max=128,
+                 bg=(0.0, 0.0, 0.0), table=None, brick=0, grid_res=None, stream=None):
+        self.grid, self.table = grid, table
+        self.p_xy, self.p_xz, self.p_yz = p_xy, p_xz, p_yz
+        self.occ, self.mlp = occ, mlp
+        for name in ("grid", "p_xy", "p_xz", "p_yz", "occ", "mlp"):
+            _require_cuda(getattr(self, name), name)
+        if table is not None:
+            _require_cuda(table, "table")
+        dt = grid.dtype
+        if dt not in (torch.float32, torch.bfloat16) or any(t.dtype != dt for t in (p_xy, p_xz, p_yz)):
+            raise OmerfError("grid and planes must share one dtype, float32 or bfloat16")
+        if occ.dtype != torch.float32 or mlp.dtype != torch.float32 or mlp.numel() != MLP_NPARAM:
+            raise OmerfError("occ and mlp must be float32; mlp has 883 values")
+        self.device = grid.device
+        self.brick = int(brick)
+        if grid_res is None:
+            if self.brick:
+                raise OmerfError("grid_res is required for a brick grid")
+            grid_res = tuple(grid.shape[:3])
+        self.grid_res = tuple(int(v) for v in grid_res)
+        self.plane_res = (int(p_xy.shape[0]), int(p_xy.shape[1]), int(p_xz.shape[1]))
+        self.occ_res = int(occ.shape[0])
+        self.aabb = tuple(float(np.float32(v)) for v in aabb)
+        self.step, self.eps, self.t_thr, self.n_max = float(step), float(eps), float(t_thr), int(n_max)
+        self.bg = tuple(float(v) for v in bg)
+        d = _SceneDesc()
+        d.aabb[:] = list(self.aabb)
+        d.grid_res[:] = list(self.grid_res)
+        d.brick = self.brick
+        d.n_bricks = int(grid.shape[0]) if self.brick else 0
+        d.plane_res[:] = list(self.plane_res)
+        d.occ_res = self.occ_res
+        d.feat_dtype = OMERF_BF16 if dt == torch.bfloat16 else OMERF_F32
+        d.step, d.eps_occ, d.t_thr = self.step, self.eps, self.t_thr
+        d.bg[:] = list(self.bg)
+        d.n_max = self.n_max
+        d.grid = grid.data_ptr()
+        d.brick_table = table.data_ptr() if table is not None else None
+        d.plane_xy, d.plane_xz, d.plane_yz = p_xy.data_ptr(), p_xz.data_ptr(), p_yz.data_ptr()
+        d.occ, d.mlp = occ.data_ptr(), mlp.data_ptr()
+        self._desc = d
+        h = ctypes.c_void_p()
+        _check(lib().omerf_scene_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)), "omerf_scene_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def feat_dtype(self):
+        return self.grid.dtype
+
+    def update(self, stream=None):
+        """Recompute the occupancy hull after occ changed in place."""
+        _check(lib().omerf_scene_update(self._h, _stream(stream)), "omerf_scene_update")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().omerf_scene_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_brick_table(aabb, grid_res, brick, occ: torch.Tensor, stream=None):
+    """Sec. 4.4 brick allocation on the GPU -> (int32 table [nbx, nby, nbz], n_alloc tensor)."""
+    _require_cuda(occ, "occ")
+    nb = [(int(l) + brick - 1) // brick for l in grid_res]
+    table = torch.empty(nb, dtype=torch.int32, device=occ.device)
+    n_alloc = torch.empty(1, dtype=torch.int32, device=occ.device)
+    a = (ctypes.c_float * 6)(*[float(v) for v in aabb])
+    g = (ctypes.c_int32 * 3)(*[int(v) for v in grid_res])
+    _check(lib().omerf_build_brick_table(a, g, int(brick), _ptr(occ), int(occ.shape[0]), _ptr(table),
+                                         _ptr(n_alloc), _stream(stream)), "omerf_build_brick_table")
+    return table, n_alloc
+
+
+def scene_from_synth(sc: dict, device="cuda", feat_dtype=None, table=None, stream=None, **over) -> Scene:
+    """Upload a scene dict (keys grid/table, p_xy, p_xz, p_yz, occ, mlp, spec).
+
+    For a brick grid without a pool, the brick table is built on the GPU
+    (unless ``table`` is given) and the dict's generator fills the pool.
+    """
+    spec = sc["spec"]
+    device = torch.device(device)
+    dt = feat_dtype or (torch.bfloat16 if getattr(spec, "feat_dtype", "f32") == "bf16" else torch.float32)
+    occ = torch.as_tensor(sc["occ"], dtype=torch.float32).to(device).contiguous()
+    brick = int(spec.brick) if (sc.get("grid") is None or sc.get("table") is not None) else 0
+    if brick:
+        if sc.get("grid") is not None and sc.get("table") is not None:
+            tab = torch.as_tensor(np.asarray(sc["table"], np.int32)).to(device)
+            pool = sc["grid"]
+        else:
+            if table is None:
+                tab, _ = build_brick_table(spec.aabb, spec.L, brick, occ, stream)
+                table = tab.cpu().numpy()
+            tab = torch.as_tensor(np.asarray(table, np.int32)).to(device)
+            import synth  # the generator draws the feature values of the allocated bricks
+            pool = synth.fill_brick_pool(sc, np.asarray(table))
+        grid = torch.as_tensor(pool).to(device=device, dtype=dt).contiguous()
+    else:
+        tab = None
+        grid = torch.as_tensor(sc["grid"]).to(device=device, dtype=dt).contiguous()
+    kw = dict(aabb=spec.aabb, grid=grid, table=tab, brick=brick, grid_res=spec.L,
+              p_xy=torch.as_tensor(sc["p_xy"]).to(device=device, dtype=dt).contiguous(),
+              p_xz=torch.as_tensor(sc["p_xz"]).to(device=device, dtype=dt).contiguous(),
+              p_yz=torch.as_tensor(sc["p_yz"]).to(device=device, dtype=dt).contiguous(),
+              occ=occ, mlp=torch.as_tensor(sc["mlp"], dtype=torch.float32).to(device).contiguous(),
+              step=spec.step, eps=spec.eps, t_thr=spec.t_thr, n_max=spec.n_max, stream=stream)
+    kw.update(over)
+    return Scene(**kw)
+
+
+def render(scene: Scene, camera=None, rays=None, out=None, count_out=None, stream=None, want_count=True):
+    """Forward render (Eqs. 1-4, 6-8) of a camera (dict) or of rays [n, 6].
+
+    Returns (rgb [n, 3] float32, count [n] int32 or None) on the scene's
+    device.  With ``out`` (and ``count_out``) given as CPU tensors, the
+    results are copied into them (the copy is enqueued on the stream).
+    """
+    dev = scene.device
+    cam_p = None
+    if camera is not None:
+        cs = camera_struct(camera)
+        n = cs.width * cs.height
+        cam_p = ctypes.byref(cs)
+        rays_t = None
+    else:
+        rays_t = _dev_f32(rays, dev)
+        n = int(rays_t.shape[0])
+    rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    count = torch.empty(n, dtype=torch.int32, device=dev) if (want_count or count_out is not None) else None
+    st = _stream(stream)
+    _check(lib().omerf_render(scene.handle, cam_p, _ptr(rays_t), n, _ptr(rgb), _ptr(count), st), "omerf_render")
+    if out is not None:
+        out.copy_(rgb, non_blocking=True)
+        if count_out is not None:
+            count_out.copy_(count, non_blocking=True)
+        return out, count_out
+    return rgb, count
+
+
+def ray_interval(scene: Scene, camera=None, rays=None, stream=None):
+    """Per-ray lattice range [k_lo, k_hi] scanned by the march (int32 [n, 2])."""
+    dev = scene.device
+    cam_p = None
+    if camera is not None:
+        cs = camera_struct(camera)
+        n = cs.width * cs.height
+        cam_p = ctypes.byref(cs)
+        rays_t = None
+    else:
+        rays_t = _dev_f32(rays, dev)
+        n = int(rays_t.shape[0])
+    out = torch.empty((n, 2), dtype=torch.int32, device=dev)
+    _check(lib().omerf_ray_interval(scene.handle, cam_p, _ptr(rays_t), n, _ptr(out), _stream(stream)),
+           "omerf_ray_interval")
+    return out
+
+
+def saved_bytes_per_ray() -> int:
+    return int(lib().omerf_saved_bytes_per_ray())
+
+
+def _train_inputs(scene, rays, target, smooth_dirs):
+    dev = scene.device
+    rays_t = _dev_f32(rays, dev)
+    n = int(rays_t.shape[0])
+    target_t = _dev_f32(target, dev, (n, 3))
+    if smooth_dirs is None:
+        dirs_t, K = None, 0
+    else:
+        dirs_t = _dev_f32(smooth_dirs, dev)
+        dirs_t = dirs_t.reshape(n, -1, 3)
+        K = int(dirs_t.shape[1])
+    return rays_t, target_t, dirs_t, n, K
+
+
+def _lam(lam):
+    return (ctypes.c_float * 3)(*[float(v) for v in lam])
+
+
+def train_fwd(scene, rays, target, smooth_dirs=None, lam=(1.0, 1e-2, 0.0), stream=None):
+    """Training forward: loss [4] (total, rgb, smooth, occ) and the saved state."""
+    rays_t, target_t, dirs_t, n, K = _train_inputs(scene, rays, target, smooth_dirs)
+    saved = torch.empty(max(n, 1) * saved_bytes_per_ray() // 4, dtype=torch.float32, device=scene.device)
+    loss = torch.empty(4, dtype=torch.float32, device=scene.device)
+    _check(lib().omerf_train_fwd(scene.handle, _ptr(rays_t), _ptr(target_t), _ptr(dirs_t), n, K, _lam(lam),
+                                 _ptr(saved), _ptr(loss), _stream(stream)), "omerf_train_fwd")
+    return loss, saved, (rays_t, target_t, dirs_t, n, K)
+
+
+def _zero_grads(scene):
+    z = lambda t: torch.zeros(t.shape, dtype=torch.float32, device=t.device)  # noqa: E731
+    return {"grid": z(scene.grid), "p_xy": z(scene.p_xy), "p_xz": z(scene.p_xz), "p_yz": z(scene.p_yz),
+            "occ": z(scene.occ), "mlp": z(scene.mlp)}
+
+
+def train_bwd(scene, saved, inputs, lam=(1.0, 1e-2, 0.0), grad_scale=None, grads=None, stream=None):
+    """Training backward: accumulates grad_scale * dL/dparam into ``grads`` (float32)."""
+    rays_t, target_t, dirs_t, n, K = inputs
+    if grads is None:
+        grads = _zero_grads(scene)
+    gs = None
+    if grad_scale is not None:
+        gs = torch.as_tensor(grad_scale, dtype=torch.float32, device=scene.device).reshape(1).contiguous()
+    _check(lib().omerf_train_bwd(scene.handle, _ptr(rays_t), _ptr(target_t), _ptr(dirs_t), n, K, _lam(lam),
+                                 _ptr(saved), _ptr(gs), _ptr(grads["grid"]), _ptr(grads["p_xy"]),
+                                 _ptr(grads["p_xz"]), _ptr(grads["p_yz"]), _ptr(grads["occ"]),
+                                 _ptr(grads["mlp"]), _stream(stream)), "omerf_train_bwd")
+    return grads
+
+
+def train_step(scene, rays, target, smooth_dirs=None, lam=(1.0, 1e-2, 0.0), grads=None, saved=None,
+               stream=None):
+    """One fused forward + backward: returns {"loss": [4] tensor, "grads": dict}."""
+    rays_t, target_t, dirs_t, n, K = _train_inputs(scene, rays, target, smooth_dirs)
+    if saved is None:
+        saved = torch.empty(max(n, 1) * saved_bytes_per_ray() // 4, dtype=torch.float32, device=scene.device)
+    loss = torch.empty(4, dtype=torch.float32, device=scene.device)
+    if grads is None:
+        grads = _zero_grads(scene)
+    _check(lib().omerf_train_step(scene.handle, _ptr(rays_t), _ptr(target_t), _ptr(dirs_t), n, K, _lam(lam),
+                                  _ptr(saved), _ptr(loss), _ptr(grads["grid"]), _ptr(grads["p_xy"]),
+                                  _ptr(grads["p_xz"]), _ptr(grads["p_yz"]), _ptr(grads["occ"]),
+                                  _ptr(grads["mlp"]), _stream(stream)), "omerf_train_step")
+    return {"loss": loss, "grads": grads, "saved": saved}
+
+
+def sync(stream=None, timeout_ms=-1):
+    """Bounded wait for a stream (raises OmerfError on timeout or CUDA error)."""
+    _check(lib().omerf_sync(_stream(stream), int(timeout_ms)), "omerf_sync")
+
+
+class TrainStep(torch.autograd.Function):
+    """Differentiable loss of Eqs. 5, 9-10, 12 over the scene's parameters.
+
+    Usage: loss = TrainStep.apply(scene, rays, target, smooth_dirs, lam,
+    scene.grid, scene.p_xy, scene.p_xz, scene.p_yz, scene.occ, scene.mlp)
+    The parameter tensors must be the scene's own tensors (the kernels read
+    them through the scene handle); their gradients are float32.
+    """
+
+    @staticmethod
+    def forward(ctx, scene, rays, target, smooth_dirs, lam, grid, p_xy, p_xz, p_yz, occ, mlp):
+        for a, b in ((grid, scene.grid), (p_xy, scene.p_xy), (p_xz, scene.p_xz), (p_yz, scene.p_yz),
+                     (occ, scene.occ), (mlp, scene.mlp)):
+            if a.data_ptr() != b.data_ptr():
+                raise OmerfError("TrainStep parameters must be the scene's own tensors")
+        loss, saved, inputs = train_fwd(scene, rays, target, smooth_dirs, lam)
+        ctx.scene, ctx.saved, ctx.inputs, ctx.lam = scene, saved, inputs, lam
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = train_bwd(ctx.scene, ctx.saved, ctx.inputs, ctx.lam, grad_scale=grad_out.detach().float())
+        s = ctx.scene
+
+        def cast(name):
+            t = g[name]
+            ref = getattr(s, name)
+            return t if ref.dtype == torch.float32 else t.to(ref.dtype)
+
+        return (None, None, None, None, None, cast("grid"), cast("p_xy"), cast("p_xz"), cast("p_yz"),
+                g["occ"], g["mlp"])

@@ -1,0 +1,367 @@
+// common.cuh -- device building blocks of the Oblique-MERF march (sm_103a).
+//
+// Oblique-MERF (arXiv 2404.09531):
+//   feature field   t(p) = V(p) + P_xy + P_xz + P_yz          Sec. 3, Eq. 2
+//   activations     tau = exp, c^d / f = sigmoid               Eq. 3
+//   occupancy       M(z), q = 2 power ramps, nearest cell       Sec. 4.1, Eqs. 6-7
+//   compositing     w_i = T_i M_i alpha_i                       Eqs. 1, 8
+//   deferred MLP    G(F, d), 34 -> 16 -> 16 -> 3                Eq. 4, appendix A
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace omerf {
+
+constexpr int kNch = 8;
+constexpr int kMlpParams = 883;
+constexpr int kOffW1 = 0, kOffB1 = 544, kOffW2 = 560, kOffB2 = 816, kOffW3 = 832, kOffB3 = 880;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxLattice = (1 << 24) - 1;  // t_k = k * step is exact below 2^24
+// per-ray training state: F[7], T_N, count, k_lo, k_hi, pad | dL/dF[7], dL/dT_N  (80 B)
+constexpr int kSavedFloats = 20;
+
+// Kernel-uniform scene description (passed by value, lives in the constant bank).
+struct Geo {
+  float lo[3], hi[3];      // box
+  float gs[3];             // grid: (L - 1) / (hi - lo)
+  float ps[3];             // planes: (R - 1) / (hi - lo)
+  int L[3], R[3];
+  float osx, osy;          // occupancy cells: M / (hi - lo), float32 as in the decision rule
+  int M;
+  float step, inv_eps, t_thr;
+  float bg[3];
+  int n_max;
+  int blog2;               // log2 of the brick edge (brick grids)
+  int nb[3];               // brick grid dimensions
+  const void* grid;
+  const int* table;
+  const void* pxy;
+  const void* pxz;
+  const void* pyz;
+  const float2* occ;
+  const float* mlp;
+  const float* hull;       // device [2]: min z_min, max z_max over non-empty cells
+};
+
+struct Cam {
+  float c2w[12];
+  float fx, fy, cx, cy;
+  int width, height;
+};
+
+// ---------------------------------------------------------------------------
+// rays
+// ---------------------------------------------------------------------------
+
+// Pinhole ray of pixel (px, py): float32, left to right, no fused operations.
+__device__ __forceinline__ void camera_ray(const Cam& c, int px, int py, float o[3], float d[3]) {
+  float ux = __fdiv_rn(__fsub_rn(__fadd_rn((float)px, 0.5f), c.cx), c.fx);
+  float uy = -__fdiv_rn(__fsub_rn(__fadd_rn((float)py, 0.5f), c.cy), c.fy);
+  float uz = -1.0f;
+  float dc[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+    dc[a] = __fadd_rn(__fadd_rn(__fmul_rn(c.c2w[4 * a + 0], ux), __fmul_rn(c.c2w[4 * a + 1], uy)),
+                      __fmul_rn(c.c2w[4 * a + 2], uz));
+  float nn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dc[0], dc[0]), __fmul_rn(dc[1], dc[1])),
+                                  __fmul_rn(dc[2], dc[2])));
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    d[a] = __fdiv_rn(dc[a], nn);
+    o[a] = c.c2w[4 * a + 3];
+  }
+}
+
+// Conservative lattice range [klo, khi] of a ray: the box, with z narrowed to
+// the occupancy hull, each axis padded by more than the float32 error of the
+// sample positions, plus two lattice steps.  Returns false when empty.
+__device__ __forceinline__ bool lattice_range(const Geo& g, const float o[3], const float d[3], int& klo,
+                                              int& khi) {
+  float tin = 0.0f, tout = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    float lo = g.lo[a], hi = g.hi[a];
+    if (a == 2) {
+      lo = fmaxf(lo, g.hull[0]);
+      hi = fminf(hi, g.hull[1]);
+      if (!(lo <= hi)) return false;
+    }
+    if (d[a] == 0.0f) {
+      if (o[a] < lo || o[a] > hi) return false;
+      continue;
+    }
+    float inv = 1.0f / d[a];
+    float ta = (lo - o[a]) * inv, tb = (hi - o[a]) * inv;
+    if (ta > tb) { float s = ta; ta = tb; tb = s; }
+    float pad = 1e-6f * (fmaxf(fabsf(ta), fabsf(tb)) + (fabsf(o[a]) + 1.0f) * fabsf(inv));
+    tin = fmaxf(tin, ta - pad);
+    tout = fminf(tout, tb + pad);
+  }
+  if (!(tin <= tout)) return false;
+  float kl = floorf(tin / g.step) - 2.0f;
+  float kh = ceilf(tout / g.step) + 2.0f;
+  kl = fmaxf(kl, 0.0f);
+  kh = fminf(kh, (float)kMaxLattice);
+  if (kl > kh) return false;
+  klo = (int)kl;
+  khi = (int)kh;
+  return true;
+}
+
+// The sample decision for lattice index k (float32, no fused operations):
+// inside the closed box and strictly inside the nearest cell's interval.
+__device__ __forceinline__ bool lattice_test(const Geo& g, const float o[3], const float d[3], int k,
+                                             float p[3], float2& zb, int& cell) {
+  float t = __fmul_rn((float)k, g.step);
+#pragma unroll
+  for (int a = 0; a < 3; a++) p[a] = __fadd_rn(o[a], __fmul_rn(t, d[a]));
+  if (!(p[0] >= g.lo[0] && p[0] <= g.hi[0] && p[1] >= g.lo[1] && p[1] <= g.hi[1] && p[2] >= g.lo[2] &&
+        p[2] <= g.hi[2]))
+    return false;
+  int cx = (int)floorf(__fmul_rn(__fsub_rn(p[0], g.lo[0]), g.osx));
+  int cy = (int)floorf(__fmul_rn(__fsub_rn(p[1], g.lo[1]), g.osy));
+  cx = min(max(cx, 0), g.M - 1);
+  cy = min(max(cy, 0), g.M - 1);
+  cell = cx * g.M + cy;
+  zb = __ldg(g.occ + cell);
+  return zb.x < p[2] && p[2] < zb.y;
+}
+
+// Eq. 6 with q = 2; overlapping ramps take the smaller value.  branch: 0 flat,
+// 1 lower ramp (r = (z - z_min)/eps), 2 upper ramp (r = (z_max - z)/eps).
+__device__ __forceinline__ float occupancy(const Geo& g, float z, float2 zb, int& branch, float& r) {
+  float rl = (z - zb.x) * g.inv_eps, rh = (zb.y - z) * g.inv_eps;
+  float ml = rl * rl, mh = rh * rh;
+  if (ml < 1.0f && ml <= mh) { branch = 1; r = rl; return ml; }
+  if (mh < 1.0f) { branch = 2; r = rh; return mh; }
+  branch = 0;
+  r = 0.0f;
+  return 1.0f;
+}
+
+// ---------------------------------------------------------------------------
+// feature gather (Eq. 2): 8 grid corners + 3 x 4 plane texels, 8 channels each
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void axis_coord(float x, float lo, float s, int L, int& i, float& w) {
+  float u = (x - lo) * s;
+  u = fminf(fmaxf(u, 0.0f), (float)(L - 1));
+  i = min((int)u, L - 2);
+  w = u - (float)i;
+}
+
+template <class FT>
+struct Texel;
+
+template <>
+struct Texel<float> {
+  static constexpr int kBytes = 32;
+  __device__ __forceinline__ static void load(const void* base, int elem, float v[8]) {
+    const float4* q = reinterpret_cast<const float4*>(static_cast<const float*>(base) + elem);
+    float4 a = __ldg(q), b = __ldg(q + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+};
+
+template <>
+struct Texel<__nv_bfloat16> {
+  static constexpr int kBytes = 16;
+  __device__ __forceinline__ static void load(const void* base, int elem, float v[8]) {
+    const uint4* q = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + elem);
+    uint4 a = __ldg(q);
+    unsigned w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      v[2 * i] = __uint_as_float(w[i] << 16);
+      v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+  }
+};
+
+// Element offsets of the 8 grid corners (-1 for an unallocated brick) and
+// their trilinear weights, corner order (dx, dy, dz) with dz fastest.
+template <bool SPARSE>
+__device__ __forceinline__ void grid_stencil(const Geo& g, const float p[3], int off[8], float w[8]) {
+  int i[3];
+  float f[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) axis_coord(p[a], g.lo[a], g.gs[a], g.L[a], i[a], f[a]);
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    int da = (c >> 2) & 1, db = (c >> 1) & 1, dc = c & 1;
+    w[c] = (da ? f[0] : 1.0f - f[0]) * (db ? f[1] : 1.0f - f[1]) * (dc ? f[2] : 1.0f - f[2]);
+  }
+  if (!SPARSE) {
+    const int base = ((i[0] * g.L[1] + i[1]) * g.L[2] + i[2]) * kNch;
+    const int sz = kNch, sy = g.L[2] * kNch, sx = g.L[1] * g.L[2] * kNch;
+#pragma unroll
+    for (int c = 0; c < 8; c++) off[c] = base + ((c >> 2) & 1) * sx + ((c >> 1) & 1) * sy + (c & 1) * sz;
+  } else {
+    const int s = g.blog2, m = (1 << s) - 1, B = 1 << s;
+    int bi = i[0] >> s, bj = i[1] >> s, bk = i[2] >> s;
+    if ((i[0] & m) != m && (i[1] & m) != m && (i[2] & m) != m) {
+      const int b = __ldg(g.table + (bi * g.nb[1] + bj) * g.nb[2] + bk);
+      const int base = ((((b * B + (i[0] & m)) * B + (i[1] & m)) * B) + (i[2] & m)) * kNch;
+      const int sz = kNch, sy = B * kNch, sx = B * B * kNch;
+#pragma unroll
+      for (int c = 0; c < 8; c++)
+        off[c] = b < 0 ? -1 : base + ((c >> 2) & 1) * sx + ((c >> 1) & 1) * sy + (c & 1) * sz;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        int vi = i[0] + ((c >> 2) & 1), vj = i[1] + ((c >> 1) & 1), vk = i[2] + (c & 1);
+        const int b = __ldg(g.table + ((vi >> s) * g.nb[1] + (vj >> s)) * g.nb[2] + (vk >> s));
+        off[c] = b < 0 ? -1 : ((((b * B + (vi & m)) * B + (vj & m)) * B) + (vk & m)) * kNch;
+      }
+    }
+  }
+}
+
+// Element offsets and bilinear weights of the 12 plane texels: XY, XZ, YZ.
+__device__ __forceinline__ void plane_stencil(const Geo& g, const float p[3], int off[12], float w[12]) {
+  int i[3];
+  float f[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) axis_coord(p[a], g.lo[a], g.ps[a], g.R[a], i[a], f[a]);
+  const int U[3] = {0, 0, 1}, V[3] = {1, 2, 2};
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    int u = U[q], v = V[q];
+    const int base = (i[u] * g.R[v] + i[v]) * kNch;
+    const int su = g.R[v] * kNch;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      int da = (c >> 1) & 1, db = c & 1;
+      off[4 * q + c] = base + da * su + db * kNch;
+      w[4 * q + c] = (da ? f[u] : 1.0f - f[u]) * (db ? f[v] : 1.0f - f[v]);
+    }
+  }
+}
+
+__device__ __forceinline__ const void* plane_base(const Geo& g, int q) {
+  return q == 0 ? g.pxy : (q == 1 ? g.pxz : g.pyz);
+}
+
+template <class FT, bool SPARSE>
+__device__ __forceinline__ void gather_features(const Geo& g, const float p[3], float t[8]) {
+  int goff[8], poff[12];
+  float gw[8], pw[12];
+  grid_stencil<SPARSE>(g, p, goff, gw);
+  plane_stencil(g, p, poff, pw);
+#pragma unroll
+  for (int c = 0; c < 8; c++) t[c] = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    float v[8];
+    if (goff[c] >= 0) {
+      Texel<FT>::load(g.grid, goff[c], v);
+#pragma unroll
+      for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(gw[c], v[ch], t[ch]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    const void* P = plane_base(g, q);
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      float v[8];
+      Texel<FT>::load(P, poff[4 * q + c], v);
+#pragma unroll
+      for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(pw[4 * q + c], v[ch], t[ch]);
+    }
+  }
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// Eq. 3 and the opacity of Eq. 1 for one evaluated sample.
+struct SampleAct {
+  float Mv, sigma, alpha, ah;
+  float x[7];
+  int branch;
+  float r;
+};
+
+__device__ __forceinline__ void activate(const Geo& g, const float t[8], float z, float2 zb, SampleAct& s) {
+  s.Mv = occupancy(g, z, zb, s.branch, s.r);
+  float tau = expf(t[0]);
+  s.sigma = tau * g.step;
+  s.alpha = -expm1f(-s.sigma);
+  s.ah = s.Mv * s.alpha;
+#pragma unroll
+  for (int c = 0; c < 7; c++) s.x[c] = sigmoidf_(t[c + 1]);
+}
+
+// ---------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(kFull, v, s);
+  return v;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// deferred MLP G(F, d) in float32 (thread per ray), weights in shared memory
+// ---------------------------------------------------------------------------
+struct MlpCache {
+  float x[34];
+  float a1[16], a2[16];
+  float y[3];
+};
+
+__device__ __forceinline__ void view_encoding(const float d[3], float* x) {
+  x[0] = d[0];
+  x[1] = d[1];
+  x[2] = d[2];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    float f = (float)(1 << k);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      float s, c;
+      sincosf(f * d[a], &s, &c);
+      x[3 + 6 * k + a] = s;
+      x[3 + 6 * k + 3 + a] = c;
+    }
+  }
+}
+
+__device__ __forceinline__ void mlp_forward(const float* __restrict__ W, const float F[7], const float d[3],
+                                            MlpCache& c) {
+#pragma unroll
+  for (int i = 0; i < 7; i++) c.x[i] = F[i];
+  view_encoding(d, c.x + 7);
+#pragma unroll
+  for (int j = 0; j < 16; j++) {
+    float a = W[kOffB1 + j];
+#pragma unroll
+    for (int i = 0; i < 34; i++) a = fmaf(W[kOffW1 + j * 34 + i], c.x[i], a);
+    c.a1[j] = a;
+  }
+#pragma unroll
+  for (int j = 0; j < 16; j++) {
+    float a = W[kOffB2 + j];
+#pragma unroll
+    for (int i = 0; i < 16; i++) a = fmaf(W[kOffW2 + j * 16 + i], fmaxf(c.a1[i], 0.0f), a);
+    c.a2[j] = a;
+  }
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    float a = W[kOffB3 + j];
+#pragma unroll
+    for (int i = 0; i < 16; i++) a = fmaf(W[kOffW3 + j * 16 + i], fmaxf(c.a2[i], 0.0f), a);
+    c.y[j] = sigmoidf_(a);
+  }
+}
+
+}  // namespace omerf

@@ -1,0 +1,489 @@
+// march_bwd.cu -- training backward: deferred-MLP backward and the
+// recompute-in-backward march (sm_103a).
+//
+// Per bundle of 32 consecutive rays (one warp):
+//  1. each lane recomputes its ray's deferred MLP G(F, d) (Eq. 4) and the
+//     smoothness evaluations G(F, s_k) (Eqs. 9-10), forms dL/dC of the
+//     Charbonnier loss (Eq. 12) and backpropagates to dL/dF, dL/dT_N and the
+//     MLP weights.  Weight gradients are staged per warp in shared memory and
+//     summed over the 32 rays by lanes that own disjoint weights;
+//  2. the warp re-marches every ray of the bundle exactly like the forward
+//     (same lattice windows, same product scan) for its saved sample count,
+//     and converts dL/dF into per-sample gradients:
+//        dL/d(alpha_hat_i) = T_i g.x_i - [g.(F - A_<=i) + g_T T_N] / (1 - alpha_hat_i)
+//     (A_<=i = prefix sum of w x, by a lane scan), then chains through Eq. 3
+//     and Eq. 6 and scatter-adds into the grid, planes and z-bounds with
+//     vector float atomics.  No per-sample state is stored between passes.
+#include "internal.h"
+
+namespace omerf {
+
+constexpr int kBwdThreads = 128;   // 4 warps per CTA
+constexpr int kRow = 101;          // staged floats per ray: x 34, h1 16, h2 16, g1 16, g2 16, g3 3
+constexpr int kOwned = (kMlpParams + 31) / 32;  // weights owned per lane (28)
+
+struct BwdArgs {
+  const float* rays;
+  const float* target;
+  const float* dirs;
+  int K;
+  long n, n_bundles;
+  float lam_rgb, lam_smooth;  // divided by n
+  float* saved;
+  const float* grad_scale;
+  float* g_grid;
+  float* g_xy;
+  float* g_xz;
+  float* g_yz;
+  float* g_occ;
+  float* g_mlp;
+  unsigned* counter;
+};
+
+// Deferred MLP forward for one lane's ray, writing the staged row
+// (x, h1 = relu(a1), h2 = relu(a2)) to shared memory; returns y.  Output
+// units are produced one at a time (outer loops not unrolled) so that only
+// one layer input lives in registers.
+__device__ __forceinline__ void mlp_forward_row(const float* __restrict__ W, const float F[7], const float d[3],
+                                                float* __restrict__ row, float y[3]) {
+  {
+    float x[34];
+#pragma unroll
+    for (int i = 0; i < 7; i++) x[i] = F[i];
+    view_encoding(d, x + 7);
+#pragma unroll
+    for (int i = 0; i < 34; i++) row[i] = x[i];
+#pragma unroll 1
+    for (int j = 0; j < 16; j++) {
+      float a = W[kOffB1 + j];
+#pragma unroll
+      for (int i = 0; i < 34; i++) a = fmaf(W[kOffW1 + j * 34 + i], x[i], a);
+      row[34 + j] = fmaxf(a, 0.0f);
+    }
+  }
+  {
+    float h1[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) h1[i] = row[34 + i];
+#pragma unroll 1
+    for (int j = 0; j < 16; j++) {
+      float a = W[kOffB2 + j];
+#pragma unroll
+      for (int i = 0; i < 16; i++) a = fmaf(W[kOffW2 + j * 16 + i], h1[i], a);
+      row[50 + j] = fmaxf(a, 0.0f);
+    }
+  }
+  float h2[16];
+#pragma unroll
+  for (int i = 0; i < 16; i++) h2[i] = row[50 + i];
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    float a = W[kOffB3 + j];
+#pragma unroll
+    for (int i = 0; i < 16; i++) a = fmaf(W[kOffW3 + j * 16 + i], h2[i], a);
+    y[j] = sigmoidf_(a);
+  }
+}
+
+// Backprop gy through the staged evaluation: writes the layer deltas
+// (g1, g2, g3) into the row and adds the feature-input gradient into gF.
+// A ReLU unit is active iff its staged output is positive.
+__device__ __forceinline__ void mlp_backward_row(const float* __restrict__ W, float* __restrict__ row,
+                                                 const float y[3], const float gy[3], float gF[7]) {
+  float g3[3];
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    g3[j] = gy[j] * y[j] * (1.0f - y[j]);
+    row[98 + j] = g3[j];
+  }
+#pragma unroll 1
+  for (int i = 0; i < 16; i++) {
+    float a = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; j++) a = fmaf(W[kOffW3 + j * 16 + i], g3[j], a);
+    row[82 + i] = row[50 + i] > 0.0f ? a : 0.0f;
+  }
+  {
+    float g2[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) g2[j] = row[82 + j];
+#pragma unroll 1
+    for (int i = 0; i < 16; i++) {
+      float a = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 16; j++) a = fmaf(W[kOffW2 + j * 16 + i], g2[j], a);
+      row[66 + i] = row[34 + i] > 0.0f ? a : 0.0f;
+    }
+  }
+  float g1[16];
+#pragma unroll
+  for (int j = 0; j < 16; j++) g1[j] = row[66 + j];
+#pragma unroll
+  for (int i = 0; i < 7; i++) {
+    float a = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 16; j++) a = fmaf(W[kOffW1 + j * 34 + i], g1[j], a);
+    gF[i] += a;
+  }
+}
+
+__device__ __forceinline__ void zero_row(float* __restrict__ row) {
+#pragma unroll 4
+  for (int i = 0; i < kRow; i++) row[i] = 0.0f;
+}
+
+// Sum the staged weight gradient of the warp's 32 rows into the warp's
+// accumulator; lane l owns weights l, l + 32, ...
+__device__ __forceinline__ void accumulate_rows(const float* __restrict__ rows, int lane, float* __restrict__ dW) {
+  __syncwarp();
+#pragma unroll 1
+  for (int m = 0; m < kOwned; m++) {
+    const int w = lane + 32 * m;
+    if (w >= kMlpParams) break;
+    int da, aa;  // delta column, activation column (-1: bias)
+    if (w < kOffB1) { da = 66 + w / 34; aa = w % 34; }
+    else if (w < kOffW2) { da = 66 + (w - kOffB1); aa = -1; }
+    else if (w < kOffB2) { da = 82 + ((w - kOffW2) >> 4); aa = 34 + ((w - kOffW2) & 15); }
+    else if (w < kOffW3) { da = 82 + (w - kOffB2); aa = -1; }
+    else if (w < kOffB3) { da = 98 + ((w - kOffW3) >> 4); aa = 50 + ((w - kOffW3) & 15); }
+    else { da = 98 + (w - kOffB3); aa = -1; }
+    float s = 0.0f;
+    if (aa >= 0) {
+#pragma unroll 8
+      for (int r = 0; r < 32; r++) s = fmaf(rows[r * kRow + da], rows[r * kRow + aa], s);
+    } else {
+#pragma unroll 8
+      for (int r = 0; r < 32; r++) s += rows[r * kRow + da];
+    }
+    dW[w] += s;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void scatter8(float* base, int off, float w, const float dt[8]) {
+  float4* q = reinterpret_cast<float4*>(base + off);
+  atomicAdd(q, make_float4(w * dt[0], w * dt[1], w * dt[2], w * dt[3]));
+  atomicAdd(q + 1, make_float4(w * dt[4], w * dt[5], w * dt[6], w * dt[7]));
+}
+
+template <class FT, bool SPARSE>
+__device__ __forceinline__ void march_ray_bwd(const Geo& g, const BwdArgs& a, const float o[3], const float d[3],
+                                              int klo, int khi, int count, const float F[7], float TN,
+                                              const float gF[7], float gT, int lane) {
+  float T = 1.0f;
+  float A[7] = {0, 0, 0, 0, 0, 0, 0};
+  int cnt = 0;
+  for (int k = klo; k <= khi && cnt < count; k += 32) {
+    const int kk = k + lane;
+    float p[3];
+    float2 zb = make_float2(0.0f, 0.0f);
+    int cell = 0;
+    bool ok = kk <= khi && lattice_test(g, o, d, kk, p, zb, cell);
+    unsigned m = __ballot_sync(kFull, ok);
+    if (m == 0u) continue;
+    const int room = count - cnt;
+    const int rank = __popc(m & lanemask_lt());
+    if (__popc(m) > room) {
+      if (ok && rank >= room) ok = false;
+      m = __ballot_sync(kFull, ok);
+    }
+    SampleAct s;
+    s.ah = 0.0f;
+    s.alpha = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 7; c++) s.x[c] = 0.0f;
+    int goff[8], poff[12];
+    float gw[8], pw[12];
+    if (ok) {
+      grid_stencil<SPARSE>(g, p, goff, gw);
+      plane_stencil(g, p, poff, pw);
+      float t[8];
+#pragma unroll
+      for (int c = 0; c < 8; c++) t[c] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        if (goff[c] < 0) continue;
+        float v[8];
+        Texel<FT>::load(g.grid, goff[c], v);
+#pragma unroll
+        for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(gw[c], v[ch], t[ch]);
+      }
+#pragma unroll
+      for (int q = 0; q < 3; q++) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          float v[8];
+          Texel<FT>::load(plane_base(g, q), poff[4 * q + c], v);
+#pragma unroll
+          for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(pw[4 * q + c], v[ch], t[ch]);
+        }
+      }
+      activate(g, t, p[2], zb, s);
+    }
+    float P = 1.0f - s.ah;
+#pragma unroll
+    for (int sh = 1; sh < 32; sh <<= 1) {
+      const float v = __shfl_up_sync(kFull, P, sh);
+      if (lane >= sh) P *= v;
+    }
+    float Pex = __shfl_up_sync(kFull, P, 1);
+    if (lane == 0) Pex = 1.0f;
+    const float Ti = T * Pex, Tn = T * P;
+    const float w = ok ? Ti * s.ah : 0.0f;
+    // inclusive lane scan of w * x (prefix of F)
+    float Ai[7];
+#pragma unroll
+    for (int c = 0; c < 7; c++) {
+      float v = w * s.x[c];
+#pragma unroll
+      for (int sh = 1; sh < 32; sh <<= 1) {
+        const float u = __shfl_up_sync(kFull, v, sh);
+        if (lane >= sh) v += u;
+      }
+      Ai[c] = A[c] + v;
+    }
+    if (ok) {
+      float gx = 0.0f, suffix = gT * TN;
+#pragma unroll
+      for (int c = 0; c < 7; c++) {
+        gx = fmaf(gF[c], s.x[c], gx);
+        suffix = fmaf(gF[c], F[c] - Ai[c], suffix);
+      }
+      const bool last = (cnt + rank) == count - 1;
+      const float dah = last ? Ti * (gx - gT) : Ti * gx - suffix / (1.0f - s.ah);
+      const float dsig = dah * s.Mv * (1.0f - s.alpha);
+      float dt[8];
+      dt[0] = dsig * s.sigma;
+#pragma unroll
+      for (int c = 0; c < 7; c++) dt[c + 1] = w * gF[c] * s.x[c] * (1.0f - s.x[c]);
+      if (a.g_occ && s.branch != 0) {
+        const float dM = dah * s.alpha;
+        const float dz = (s.branch == 1 ? -2.0f : 2.0f) * s.r * g.inv_eps;
+        atomicAdd(a.g_occ + 2 * cell + (s.branch == 1 ? 0 : 1), dM * dz);
+      }
+      if (a.g_grid) {
+#pragma unroll
+        for (int c = 0; c < 8; c++)
+          if (goff[c] >= 0) scatter8(a.g_grid, goff[c], gw[c], dt);
+      }
+      float* gp[3] = {a.g_xy, a.g_xz, a.g_yz};
+#pragma unroll
+      for (int q = 0; q < 3; q++) {
+        if (!gp[q]) continue;
+#pragma unroll
+        for (int c = 0; c < 4; c++) scatter8(gp[q], poff[4 * q + c], pw[4 * q + c], dt);
+      }
+    }
+    const int lastlane = 31 - __clz(m);
+    T = __shfl_sync(kFull, Tn, lastlane);
+#pragma unroll
+    for (int c = 0; c < 7; c++) A[c] = __shfl_sync(kFull, Ai[c], lastlane);
+    cnt += __popc(m);
+  }
+}
+
+// Kernel 1: per-ray deferred-MLP backward.  Writes dL/dF (7) and dL/dT_N
+// into the ray's saved state and adds the MLP weight gradient.
+__global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, const BwdArgs a) {
+  extern __shared__ float smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* sW = smem;                                   // 884: MLP weights
+  float* sDW = smem + 884 + warp * 884;               // 884 per warp: weight-gradient sums
+  float* rows = smem + 884 * (1 + kBwdThreads / 32) + warp * 32 * kRow;
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sW[i] = g.mlp[i];
+  for (int i = threadIdx.x; i < 884 * (kBwdThreads / 32); i += blockDim.x) smem[884 + i] = 0.0f;
+  __syncthreads();
+  const float gs = a.grad_scale ? __ldg(a.grad_scale) : 1.0f;
+  const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+  for (long b = (long)blockIdx.x * (blockDim.x >> 5) + warp; b < a.n_bundles; b += nwarps) {
+    const long rid = b * 32 + lane;
+    const bool valid = rid < a.n;
+    float d[3] = {0, 0, 1};
+    float F[7] = {0, 0, 0, 0, 0, 0, 0}, TN = 1.0f;
+    int cnt = 0;
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) d[c] = __ldg(a.rays + 6 * rid + 3 + c);
+      const float4* sv = reinterpret_cast<const float4*>(a.saved + (long)kSavedFloats * rid);
+      const float4 s0 = __ldg(sv), s1 = __ldg(sv + 1), s2 = __ldg(sv + 2);
+      F[0] = s0.x; F[1] = s0.y; F[2] = s0.z; F[3] = s0.w;
+      F[4] = s1.x; F[5] = s1.y; F[6] = s1.z; TN = s1.w;
+      cnt = __float_as_int(s2.x);
+    }
+    const bool live = valid && cnt > 0;
+    float* row = rows + lane * kRow;
+    float gF[7] = {0, 0, 0, 0, 0, 0, 0};
+    float gC[3] = {0, 0, 0}, yd[3] = {0, 0, 0}, gyd[3] = {0, 0, 0};
+    if (live) {
+      mlp_forward_row(sW, F, d, row, yd);
+      float e[3], e2 = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        e[j] = F[j] + yd[j] + TN * g.bg[j] - __ldg(a.target + 3 * rid + j);
+        e2 = fmaf(e[j], e[j], e2);
+      }
+      const float inv_ell = 1.0f / sqrtf(e2 + 1e-6f);
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        gC[j] = gs * a.lam_rgb * e[j] * inv_ell;
+        gyd[j] = gC[j];
+      }
+    }
+    // smoothness evaluations (Eqs. 9-10): each one is backpropagated and staged
+    const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int k = 0; k < a.K; k++) {
+      if (live) {
+        const float* sp = a.dirs + 3 * ((long)rid * a.K + k);
+        float sv[3] = {__ldg(sp), __ldg(sp + 1), __ldg(sp + 2)};
+        const float sn = sqrtf(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
+        const float S = (d[0] * sv[0] + d[1] * sv[1] + d[2] * sv[2]) / (dn * sn);
+        float sh[3] = {sv[0] / sn, sv[1] / sn, sv[2] / sn};
+        float ys[3], gys[3];
+        mlp_forward_row(sW, F, sh, row, ys);
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          gys[j] = gs * a.lam_smooth * 2.0f * S * (ys[j] - yd[j]);
+          gyd[j] -= gys[j];
+        }
+        mlp_backward_row(sW, row, ys, gys, gF);
+      } else {
+        zero_row(row);
+      }
+      accumulate_rows(rows, lane, sDW);
+    }
+    if (live) {
+      float y[3];
+      mlp_forward_row(sW, F, d, row, y);
+      mlp_backward_row(sW, row, y, gyd, gF);
+    } else {
+      zero_row(row);
+    }
+    accumulate_rows(rows, lane, sDW);
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < 3; j++) gF[j] += gC[j];
+      const float gT = gC[0] * g.bg[0] + gC[1] * g.bg[1] + gC[2] * g.bg[2];
+      float4* sv = reinterpret_cast<float4*>(a.saved + (long)kSavedFloats * rid);
+      sv[3] = make_float4(gF[0], gF[1], gF[2], gF[3]);
+      sv[4] = make_float4(gF[4], gF[5], gF[6], gT);
+    }
+  }
+  // weight gradients: per-warp sums -> CTA sum -> one global add per CTA
+  __syncthreads();
+  if (a.g_mlp) {
+    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
+      float v = 0.0f;
+      for (int w = 0; w < kBwdThreads / 32; w++) v += smem[884 + w * 884 + i];
+      atomicAdd(a.g_mlp + i, v);
+    }
+  }
+}
+
+// Kernel 2: re-march every ray (one warp per bundle of 32 rays, persistent)
+// and scatter the per-sample gradients.
+template <class FT, bool SPARSE>
+__global__ void __launch_bounds__(kThreads) march_bwd_kernel(const Geo g, const BwdArgs a) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned b = 0;
+    if (lane == 0) b = atomicAdd(a.counter, 1u);
+    b = __shfl_sync(kFull, b, 0);
+    if (b >= a.n_bundles) break;
+    const long rid = (long)b * 32 + lane;
+    const bool valid = rid < a.n;
+    float o[3] = {0, 0, 0}, d[3] = {0, 0, 1};
+    int cnt = 0;
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        o[c] = __ldg(a.rays + 6 * rid + c);
+        d[c] = __ldg(a.rays + 6 * rid + 3 + c);
+      }
+      cnt = __float_as_int(__ldg(a.saved + (long)kSavedFloats * rid + 8));
+    }
+    unsigned todo = __ballot_sync(kFull, valid && cnt > 0);
+    while (todo) {
+      const int r = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const long rr = b * 32l + r;
+      const float* sv = a.saved + (long)kSavedFloats * rr;
+      float ro[3], rd[3], rF[7], rg[7];
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        ro[c] = __shfl_sync(kFull, o[c], r);
+        rd[c] = __shfl_sync(kFull, d[c], r);
+      }
+#pragma unroll
+      for (int c = 0; c < 7; c++) {
+        rF[c] = __ldg(sv + c);
+        rg[c] = __ldg(sv + 12 + c);
+      }
+      const float rTN = __ldg(sv + 7), rgT = __ldg(sv + 19);
+      const int rcnt = __float_as_int(__ldg(sv + 8));
+      const int rklo = __float_as_int(__ldg(sv + 9)), rkhi = __float_as_int(__ldg(sv + 10));
+      march_ray_bwd<FT, SPARSE>(g, a, ro, rd, rklo, rkhi, rcnt, rF, rTN, rg, rgT, lane);
+    }
+  }
+}
+
+template <class FT, bool SPARSE>
+static cudaError_t launch_bwd_variant(const omerf_scene* s, const BwdArgs& a, cudaStream_t stream) {
+  auto kern = march_bwd_kernel<FT, SPARSE>;
+  static int blocks[64] = {0};
+  const int dev = s->device & 63;
+  if (blocks[dev] == 0) blocks[dev] = persistent_blocks((const void*)kern, kThreads, 0, s->num_sms);
+  long want = (a.n_bundles + (kThreads / 32) - 1) / (kThreads / 32);
+  int grid = (int)(want < blocks[dev] ? want : blocks[dev]);
+  if (grid < 1) grid = 1;
+  kern<<<grid, kThreads, 0, stream>>>(s->geo, a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_mlp_bwd(const omerf_scene* s, const BwdArgs& a, cudaStream_t stream) {
+  const size_t smem = (size_t)(884 * (1 + kBwdThreads / 32) + (kBwdThreads / 32) * 32 * kRow) * sizeof(float);
+  static int blocks[64] = {0};
+  const int dev = s->device & 63;
+  if (blocks[dev] == 0) {
+    cudaFuncSetAttribute((const void*)mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    blocks[dev] = persistent_blocks((const void*)mlp_bwd_kernel, kBwdThreads, smem, s->num_sms);
+  }
+  long want = (a.n_bundles + (kBwdThreads / 32) - 1) / (kBwdThreads / 32);
+  int grid = (int)(want < blocks[dev] ? want : blocks[dev]);
+  if (grid < 1) grid = 1;
+  mlp_bwd_kernel<<<grid, kBwdThreads, smem, stream>>>(s->geo, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_march_bwd(const omerf_scene* s, const float* rays, const float* target, const float* dirs,
+                             long n, int K, const float lam[3], float* saved, const float* grad_scale,
+                             float* g_grid, float* g_xy, float* g_xz, float* g_yz, float* g_occ, float* g_mlp,
+                             cudaStream_t stream) {
+  BwdArgs a{};
+  a.rays = rays;
+  a.target = target;
+  a.dirs = dirs;
+  a.K = K;
+  a.n = n;
+  a.n_bundles = (n + 31) / 32;
+  a.lam_rgb = n > 0 ? lam[0] / (float)n : 0.0f;
+  a.lam_smooth = n > 0 ? lam[1] / (float)n : 0.0f;
+  a.saved = saved;
+  a.grad_scale = grad_scale;
+  a.g_grid = g_grid;
+  a.g_xy = g_xy;
+  a.g_xz = g_xz;
+  a.g_yz = g_yz;
+  a.g_occ = g_occ;
+  a.g_mlp = g_mlp;
+  if (a.n_bundles == 0) return cudaSuccess;
+  cudaError_t e = launch_mlp_bwd(s, a, stream);
+  if (e != cudaSuccess) return e;
+  a.counter = next_counter(s, stream);
+  const bool bf16 = s->desc.feat_dtype == OMERF_BF16;
+  const bool sparse = s->desc.brick > 0;
+  if (bf16) return sparse ? launch_bwd_variant<__nv_bfloat16, true>(s, a, stream)
+                          : launch_bwd_variant<__nv_bfloat16, false>(s, a, stream);
+  return sparse ? launch_bwd_variant<float, true>(s, a, stream) : launch_bwd_variant<float, false>(s, a, stream);
+}
+
+}  // namespace omerf

@@ -52,6 +52,7 @@ class SceneSpec:
     fov_y_deg: float = 45.0
     cam_dist: float = 2.5
     feat_dtype: str = "f32"  # storage type of grid and planes on the GPU
+    lookat_range: float = 0.5  # camera targets uniform in [-r, r]^2 at z = 0
 
 
 CONFIGS = {
@@ -62,8 +63,8 @@ CONFIGS = {
     # Forward render 1920x1080 x 8 oblique cameras, sparse 512x512x32 grid, FP32.
     2: SceneSpec("render-1920x1080x8-oblique-city-fp32", 2, (-1.0, 1.0, -1.0, 1.0, -0.0625, 0.0625),
                  (512, 512, 32), 8, (2048, 2048, 128), 256, 1.0 / 2048, 512, 0.002, 0.006,
-                 city=True, city_radius=0.62, n_cams=8, width=1920, height=1080,
-                 fov_y_deg=50.0, cam_dist=1.5),
+                 city=True, city_radius=0.555, n_cams=8, width=1920, height=1080,
+                 fov_y_deg=50.0, cam_dist=0.6, lookat_range=0.25),
     # Training fwd+bwd on the config-1 scene, 2^18 rays from 16 cameras.
     3: SceneSpec("train-2^18-rays-heightfield-fp32", 3, (-1.0, 1.0, -1.0, 1.0, -0.125, 0.125),
                  (64, 64, 16), 0, (256, 256, 32), 32, 1.0 / 256, 128, 0.01, 0.03,
@@ -71,8 +72,8 @@ CONFIGS = {
     # BF16 render 3840x2160 x 4 cameras, sparse 1024x1024x64 grid.
     4: SceneSpec("render-3840x2160x4-oblique-city-bf16", 4, (-1.0, 1.0, -1.0, 1.0, -0.0625, 0.0625),
                  (1024, 1024, 64), 8, (4096, 4096, 256), 512, 1.0 / 2048, 512, 0.002, 0.006,
-                 city=True, city_radius=0.5, n_cams=4, width=3840, height=2160,
-                 fov_y_deg=50.0, cam_dist=1.5, feat_dtype="bf16"),
+                 city=True, city_radius=0.63, n_cams=4, width=3840, height=2160,
+                 fov_y_deg=50.0, cam_dist=0.6, lookat_range=0.3, feat_dtype="bf16"),
     # Large training: 2^20 rays from 64 cameras, BF16 features with FP32 master copy.
     5: SceneSpec("train-2^20-rays-heightfield-bf16", 5, (-1.0, 1.0, -1.0, 1.0, -0.125, 0.125),
                  (64, 64, 16), 0, (256, 256, 32), 32, 1.0 / 256, 128, 0.01, 0.03,
@@ -282,7 +283,7 @@ def make_cameras(cfg: int | SceneSpec, n: int | None = None, seed: int | None = 
         else:
             pitch = rng.uniform(30.0, 60.0)
             yaw = rng.uniform(0.0, 360.0)
-            t = rng.uniform(-0.5, 0.5, 2)
+            t = rng.uniform(-spec.lookat_range, spec.lookat_range, 2)
             target = (t[0], t[1], 0.0)
         c2w = _look_at_pose(pitch, yaw, target, spec.cam_dist)
         cams.append({"c2w": c2w.astype(np.float32), "fx": np.float32(f), "fy": np.float32(f),

@@ -1,0 +1,78 @@
+"""The C ABI library loads, exports every entry point declared in
+include/omerf.h, and rejects bad arguments on the host.  CPU only: no call here
+launches a kernel."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "omerf.h")
+LIB = os.path.join(ROOT, "paper_2404_09531_gb300", "libomerf.so")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(omerf_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(LIB):
+        import __graft_entry__
+        __graft_entry__.build()
+    import paper_2404_09531_gb300 as om
+    return om.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("omerf_scene_create", "omerf_render", "omerf_train_fwd", "omerf_train_bwd",
+                     "omerf_train_step", "omerf_ray_interval", "omerf_build_brick_table"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    raw = ctypes.CDLL(LIB)
+    for name in _declared():
+        assert hasattr(raw, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_2404_09531_gb300.binding as b
+    assert sorted(b.SIGNATURES) == _declared()
+
+
+def test_host_validation_without_gpu(lib):
+    import paper_2404_09531_gb300.binding as b
+    d = b._SceneDesc()
+    d.aabb[:] = [-1, 1, -1, 1, -0.1, 0.1]
+    d.grid_res[:] = [4, 4, 4]
+    d.plane_res[:] = [4, 4, 4]
+    d.occ_res = 2
+    d.step = 0.3  # not a power of two
+    d.eps_occ = 0.01
+    d.n_max = 16
+    d.grid = d.plane_xy = d.plane_xz = d.plane_yz = d.occ = d.mlp = 4096
+    out = ctypes.c_void_p()
+    assert lib.omerf_scene_create(ctypes.byref(d), None, ctypes.byref(out)) == -1
+    assert b"power of two" in lib.omerf_last_error()
+    d.step = 1 / 64
+    d.grid_res[:] = [1, 4, 4]
+    assert lib.omerf_scene_create(ctypes.byref(d), None, ctypes.byref(out)) == -2
+    d.grid_res[:] = [4, 4, 4]
+    d.feat_dtype = 7
+    assert lib.omerf_scene_create(ctypes.byref(d), None, ctypes.byref(out)) == -1
+    d.feat_dtype = 0
+    d.grid = 4100  # misaligned
+    assert lib.omerf_scene_create(ctypes.byref(d), None, ctypes.byref(out)) == -1
+    assert b"aligned" in lib.omerf_last_error()
+    assert lib.omerf_scene_create(None, None, ctypes.byref(out)) == -1
+    aabb = (ctypes.c_float * 6)(-1, 1, -1, 1, -1, 1)
+    res = (ctypes.c_int32 * 3)(8, 8, 8)
+    assert lib.omerf_build_brick_table(aabb, res, 3, ctypes.c_void_p(4096), 4, ctypes.c_void_p(4096),
+                                       ctypes.c_void_p(4096), None) == -1
+    assert lib.omerf_render(None, None, None, 10, None, None, None) == -1
+    assert lib.omerf_saved_bytes_per_ray() == 80

@@ -1,0 +1,210 @@
+"""GPU parity of the forward render (through the C ABI) against the FP64 oracle.
+
+Bar: per-ray sample counts bit-exact (rays the oracle marks ambiguous at the
+termination threshold are excluded and counted), FP32 rgb max-abs <= 1e-4,
+BF16 PSNR >= 45 dB.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _util import (BF16_PSNR_DB, brick_inputs, compare_render, edge_rays, gpu_scene, oracle_scene_for,
+                   psnr)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+import paper_2404_09531_gb300 as om  # noqa: E402
+
+
+def _render_np(scene, **kw):
+    rgb, cnt = om.render(scene, **kw)
+    torch.cuda.synchronize()
+    return rgb.cpu().numpy(), cnt.cpu().numpy()
+
+
+def test_config1_camera_matches_oracle():
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    cam = synth.make_cameras(1)[0]
+    rgb, cnt = _render_np(scene, camera=cam)
+    ref = oracle.render(oracle.OracleScene(sc), oracle.camera_rays(cam))
+    err, amb = compare_render(rgb, cnt, ref, what="config 1")
+    assert (cnt > 0).mean() > 0.5
+
+
+def test_camera_rays_are_the_oracle_rays():
+    """Rays generated in the kernel give the same counts as the same rays passed in."""
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    cam = synth.make_cameras(1)[0]
+    a = _render_np(scene, camera=cam)
+    b = _render_np(scene, rays=oracle.camera_rays(cam))
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[0], b[0])
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 1000, 4097])
+def test_ragged_ray_lists(n):
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    rays = edge_rays(sc["spec"], n_random=max(n, 600))[:n]
+    rgb, cnt = _render_np(scene, rays=rays)
+    ref = oracle.render(oracle.OracleScene(sc), rays)
+    compare_render(rgb, cnt, ref, what=f"n={n}")
+
+
+def test_zero_rays():
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    rgb, cnt = om.render(scene, rays=np.zeros((0, 6), np.float32))
+    assert rgb.shape == (0, 3) and cnt.shape == (0,)
+
+
+def test_edge_rays_and_background():
+    sc = synth.make_scene(1)
+    bg = (0.25, 0.5, 0.75)
+    scene = gpu_scene(sc, bg=bg)
+    rays = edge_rays(sc["spec"])
+    rgb, cnt = _render_np(scene, rays=rays)
+    ref = oracle.render(oracle.OracleScene(sc, bg=bg), rays)
+    compare_render(rgb, cnt, ref, what="edge rays")
+    empty = ref["count"] == 0
+    assert empty.any()
+    np.testing.assert_allclose(rgb[empty], np.tile(np.float32(bg), (empty.sum(), 1)), atol=0)
+
+
+def test_empty_occupancy_returns_background():
+    sc = synth.make_scene(1)
+    sc = dict(sc, occ=np.tile(np.float32([0.5, -0.5]), (32, 32, 1)))
+    bg = (0.1, 0.2, 0.3)
+    scene = gpu_scene(sc, bg=bg)
+    rgb, cnt = _render_np(scene, camera=synth.make_cameras(1)[0])
+    assert cnt.max() == 0
+    np.testing.assert_array_equal(rgb, np.tile(np.float32(bg), (rgb.shape[0], 1)))
+
+
+def test_sample_cap_and_termination():
+    sc = synth.make_scene(1)
+    sc = dict(sc, grid=sc["grid"].copy())
+    sc["grid"][..., 0] += 1.5  # dense enough that rays terminate
+    cam = synth.make_cameras(1)[0]
+    rays = oracle.camera_rays(cam)
+    for over in ({}, {"n_max": 7}, {"t_thr": 0.0}, {"t_thr": 0.05}):
+        scene = gpu_scene(sc, **over)
+        rgb, cnt = _render_np(scene, camera=cam)
+        ref = oracle.render(oracle.OracleScene(sc, **over), rays)
+        compare_render(rgb, cnt, ref, what=str(over))
+        if "n_max" in over:
+            assert cnt.max() == 7
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tiny_scenes_dense_and_brick(seed):
+    rng = np.random.default_rng(seed)
+    L = tuple(int(v) for v in rng.integers(2, 12, 3))
+    R = tuple(int(v) for v in rng.integers(2, 20, 3))
+    M = int(rng.integers(1, 9))
+    sc = synth.tiny_scene(seed=seed, L=L, R=R, M=M, step=1 / 64, eps=0.05)
+    rays = edge_rays(sc["spec"], n_random=300, seed=seed)
+    scene = gpu_scene(sc, t_thr=1e-4)
+    rgb, cnt = _render_np(scene, rays=rays)
+    ref = oracle.render(oracle.OracleScene(sc, t_thr=1e-4), rays)
+    compare_render(rgb, cnt, ref, what=f"tiny dense {L} {R} {M}")
+    # the same scene as a brick grid (brick 2 or 4)
+    B = 2 if seed % 2 else 4
+    spec = dataclasses.replace(sc["spec"], brick=B)
+    sb = dict(sc, spec=spec)
+    table = oracle.brick_table(spec, sc["occ"])
+    nb = int(table.max()) + 1
+    pool = np.zeros((max(nb, 1), B, B, B, 8), np.float32)
+    for (bi, bj, bk), b in np.ndenumerate(table):
+        if b >= 0:
+            blk = sc["grid"][bi * B:(bi + 1) * B, bj * B:(bj + 1) * B, bk * B:(bk + 1) * B]
+            pool[b, :blk.shape[0], :blk.shape[1], :blk.shape[2]] = blk
+    sb["grid"], sb["table"] = pool, table
+    scene_b = gpu_scene(sb, t_thr=1e-4)
+    rgb_b, cnt_b = _render_np(scene_b, rays=rays)
+    ref_b = oracle.render(oracle.OracleScene(sb, t_thr=1e-4), rays)
+    assert ref_b["unalloc"] == 0
+    compare_render(rgb_b, cnt_b, ref_b, what=f"tiny brick {B}")
+
+
+def test_brick_table_bit_exact():
+    for cfg in (2, 4):
+        sc = synth.make_scene(cfg)
+        spec = sc["spec"]
+        occ = torch.as_tensor(sc["occ"]).cuda()
+        table, n_alloc = om.build_brick_table(spec.aabb, spec.L, spec.brick, occ)
+        torch.cuda.synchronize()
+        ref = oracle.brick_table(spec, sc["occ"])
+        np.testing.assert_array_equal(table.cpu().numpy(), ref)
+        assert int(n_alloc.item()) == int((ref >= 0).sum())
+    spec = dataclasses.replace(synth.scene_spec(2), L=(37, 29, 11), brick=4, M=13)
+    rng = np.random.default_rng(9)
+    h = rng.uniform(-0.05, 0.04, (13, 13))
+    occ = np.stack([h - 0.004, h + 0.004], -1).astype(np.float32)
+    occ[rng.uniform(size=(13, 13)) < 0.25] = [1.0, -1.0]
+    table, _ = om.build_brick_table(spec.aabb, spec.L, spec.brick, torch.as_tensor(occ).cuda())
+    np.testing.assert_array_equal(table.cpu().numpy(), oracle.brick_table(spec, occ))
+
+
+def test_interval_holds_every_evaluated_sample():
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    rays = np.concatenate([edge_rays(sc["spec"]), oracle.camera_rays(synth.make_cameras(1)[0])])
+    kr = om.ray_interval(scene, rays=rays).cpu().numpy()
+    ref = oracle.render(oracle.OracleScene(sc, t_thr=0.0), rays)
+    hit = ref["count"] > 0
+    assert np.all(kr[hit, 0] <= ref["k_first"][hit])
+    assert np.all(kr[hit, 1] >= ref["k_last"][hit])
+    assert np.all(kr[:, 0] >= 0)
+
+
+def _config2_sample(stride=97):
+    sc = synth.make_scene(2)
+    table, pool = brick_inputs(sc)
+    cams = synth.make_cameras(2)
+    return sc, table, pool, cams, stride
+
+
+def test_config2_full_frames_sampled_pixels():
+    """1920x1080 x 8 cameras at full size, the launch the benchmark times;
+    the oracle checks every 97th pixel of every frame."""
+    sc, table, pool, cams, stride = _config2_sample()
+    scene = gpu_scene(sc, table=table)
+    osc = oracle_scene_for(sc, table=table, pool=pool)
+    for cam in cams:
+        rgb, cnt = _render_np(scene, camera=cam)
+        rays = oracle.camera_rays(cam)
+        idx = np.arange(0, rays.shape[0], stride)
+        ref = oracle.render(osc, rays[idx])
+        assert ref["unalloc"] == 0
+        compare_render(rgb[idx], cnt[idx], ref, what="config 2")
+        assert (cnt > 0).mean() > 0.2
+
+
+def test_config4_bf16_psnr():
+    """BF16 features vs the FP64 oracle on the original FP32 features (PSNR >= 45 dB)
+    and on the BF16-rounded features (arithmetic error only)."""
+    sc = synth.make_scene(4)
+    table, pool = brick_inputs(sc)
+    scene = gpu_scene(sc, table=table)
+    assert scene.feat_dtype == torch.bfloat16
+    cam = synth.make_cameras(4)[0]
+    rgb, cnt = _render_np(scene, camera=cam)
+    rays = oracle.camera_rays(cam)
+    idx = np.arange(0, rays.shape[0], 127)
+    ref = oracle.render(oracle_scene_for(sc, table=table, pool=pool), rays[idx])
+    p = psnr(rgb[idx], ref["rgb"])
+    assert p >= BF16_PSNR_DB, f"BF16 PSNR {p:.1f} dB"
+    rb = lambda a: torch.as_tensor(a).to(torch.bfloat16).float().numpy()  # noqa: E731
+    sc_b = dict(sc, p_xy=rb(sc["p_xy"]), p_xz=rb(sc["p_xz"]), p_yz=rb(sc["p_yz"]))
+    ref_b = oracle.render(oracle_scene_for(sc_b, table=table, pool=rb(pool)), rays[idx])
+    ok = (ref_b["ambiguous"] == 0) & (ref["ambiguous"] == 0)
+    assert np.array_equal(cnt[idx][ok], ref_b["count"][ok])
+    assert np.abs(rgb[idx][ok] - ref_b["rgb"][ok]).max() <= 5e-4

@@ -1,0 +1,157 @@
+"""GPU parity of the training forward + backward (through the C ABI) against the
+FP64 oracle, whose analytic gradient is pinned by central differences.
+
+Bar: loss within 1e-5 relative; per parameter tensor, gradient error
+||g_gpu - g_ref|| / ||g_ref|| <= 1e-3 and max |g_gpu - g_ref| <= 1e-3 max |g_ref|.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _util import GRAD_RTOL, gpu_scene, grad_errors
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+import paper_2404_09531_gb300 as om  # noqa: E402
+
+LAM = (1.0, 1e-2, 1e-4)
+KEYS = ("grid", "p_xy", "p_xz", "p_yz", "occ", "mlp")
+
+
+def _check_grads(res, ref, rtol=GRAD_RTOL, what=""):
+    for k in KEYS:
+        g = res["grads"][k].cpu().numpy()
+        nrel, mrel = grad_errors(g, ref["grads"][k])
+        assert nrel <= rtol and mrel <= rtol, f"{what} {k}: norm-rel {nrel:.2e}, max-rel {mrel:.2e}"
+
+
+def _run(sc, batch, lam=LAM, **over):
+    scene = gpu_scene(sc, **over)
+    res = om.train_step(scene, batch["rays"], batch["target"], batch["smooth_dirs"], lam=lam)
+    torch.cuda.synchronize()
+    ref = oracle.train(oracle.OracleScene(sc, **over), batch["rays"], batch["target"], batch["smooth_dirs"],
+                       lam=lam)
+    return scene, res, ref
+
+
+def test_config3_subset_loss_and_gradients():
+    sc = synth.make_scene(3)
+    batch = synth.make_train_batch(3, 8192)
+    batch["target"] = oracle.render(oracle.OracleScene(synth.perturb_scene(sc)), batch["rays"])["rgb"].astype(
+        np.float32)
+    scene, res, ref = _run(sc, batch)
+    loss = res["loss"].cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(loss[0], ref["loss"], rtol=1e-5)
+    np.testing.assert_allclose(loss[1:], ref["loss_terms"], rtol=1e-4, atol=1e-9)
+    _check_grads(res, ref, what="config 3")
+
+
+@pytest.mark.parametrize("K", [0, 1, 3])
+def test_smoothness_directions(K):
+    sc = synth.make_scene(3)
+    batch = synth.make_train_batch(3, 1500, K=max(K, 1), seed=11)
+    if K == 0:
+        batch["smooth_dirs"] = np.zeros((1500, 0, 3), np.float32)
+    else:
+        batch["smooth_dirs"] = batch["smooth_dirs"][:, :K]
+    scene, res, ref = _run(sc, batch, lam=(1.0, 0.1, 0.0))
+    _check_grads(res, ref, what=f"K={K}")
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tiny_scenes_all_parameters(seed):
+    """Tiny scenes whose oracle gradient is checked against central differences."""
+    sc = synth.tiny_scene(seed=seed, n_rays=64)
+    batch = {k: sc[k] for k in ("rays", "target", "smooth_dirs")}
+    _, res, ref = _run(sc, batch, lam=(1.0, 0.1, 0.01), bg=(0.2, 0.3, 0.4))
+    _check_grads(res, ref, what=f"tiny {seed}")
+
+
+def test_brick_grid_gradients():
+    sc = synth.tiny_scene(seed=5, n_rays=256, L=(10, 9, 8))
+    B = 4
+    spec = dataclasses.replace(sc["spec"], brick=B)
+    table = oracle.brick_table(spec, sc["occ"])
+    nb = int(table.max()) + 1
+    pool = np.zeros((nb, B, B, B, 8), np.float32)
+    for (bi, bj, bk), b in np.ndenumerate(table):
+        if b >= 0:
+            blk = sc["grid"][bi * B:(bi + 1) * B, bj * B:(bj + 1) * B, bk * B:(bk + 1) * B]
+            pool[b, :blk.shape[0], :blk.shape[1], :blk.shape[2]] = blk
+    sb = dict(sc, spec=spec, grid=pool, table=table)
+    batch = {k: sc[k] for k in ("rays", "target", "smooth_dirs")}
+    _, res, ref = _run(sb, batch, lam=(1.0, 0.1, 0.01))
+    _check_grads(res, ref, what="brick")
+
+
+def test_64_rays_against_central_differences():
+    """64 config-3 rays: GPU gradient vs oracle central differences on sampled parameters."""
+    sc = synth.make_scene(3)
+    batch = synth.make_train_batch(3, 64, seed=21)
+    lam = (1.0, 1e-2, 1e-4)
+    scene = gpu_scene(sc, t_thr=0.0)
+    res = om.train_step(scene, batch["rays"], batch["target"], batch["smooth_dirs"], lam=lam)
+    torch.cuda.synchronize()
+    osc = oracle.OracleScene(sc, t_thr=0.0)
+    base = oracle.train(osc, batch["rays"], batch["target"], batch["smooth_dirs"], lam=lam)
+    rng = np.random.default_rng(0)
+    h = 1e-5
+    attrs = {"grid": "grid", "p_xy": "pxy", "p_xz": "pxz", "p_yz": "pyz", "occ": "occ", "mlp": "mlp"}
+    checked = 0
+    for k, attr in attrs.items():
+        ref_g = base["grads"][k].reshape(-1)
+        nz = np.nonzero(ref_g)[0]
+        flat = getattr(osc, attr).reshape(-1)
+        gpu_g = res["grads"][k].cpu().numpy().reshape(-1)
+        scale = np.abs(ref_g).max()
+        for i in rng.choice(nz, min(12, nz.size), replace=False):
+            v = flat[i]
+            flat[i] = v + h
+            rp = oracle.train(osc, batch["rays"], batch["target"], batch["smooth_dirs"], lam=lam, want_grad=False)
+            flat[i] = v - h
+            rm = oracle.train(osc, batch["rays"], batch["target"], batch["smooth_dirs"], lam=lam, want_grad=False)
+            flat[i] = v
+            if rp["signature"] != rm["signature"]:
+                continue
+            fd = (rp["loss"] - rm["loss"]) / (2 * h)
+            assert abs(gpu_g[i] - fd) <= 1e-3 * scale + 1e-6 * abs(fd), (k, i, gpu_g[i], fd)
+            checked += 1
+    assert checked >= 50
+
+
+def test_autograd_function_and_grad_scale():
+    sc = synth.make_scene(3)
+    batch = synth.make_train_batch(3, 2048, seed=3)
+    scene = gpu_scene(sc)
+    params = [scene.grid, scene.p_xy, scene.p_xz, scene.p_yz, scene.occ, scene.mlp]
+    for p in params:
+        p.requires_grad_(True)
+    loss = om.TrainStep.apply(scene, batch["rays"], batch["target"], batch["smooth_dirs"], LAM, *params)
+    (2.5 * loss).backward()
+    torch.cuda.synchronize()
+    ref = oracle.train(oracle.OracleScene(sc), batch["rays"], batch["target"], batch["smooth_dirs"], lam=LAM,
+                       grad_scale=2.5)
+    np.testing.assert_allclose(loss.item(), ref["loss"], rtol=1e-5)
+    for k, p in zip(KEYS, params):
+        nrel, mrel = grad_errors(p.grad.cpu().numpy(), ref["grads"][k])
+        assert nrel <= GRAD_RTOL and mrel <= GRAD_RTOL, (k, nrel, mrel)
+
+
+def test_bf16_features_train_against_rounded_oracle():
+    """BF16 features (FP32 master copy and FP32 gradients) vs the oracle on the
+    BF16-rounded values: only the arithmetic differs."""
+    sc = synth.make_scene(5)
+    rb = lambda a: torch.as_tensor(a).to(torch.bfloat16).float().numpy()  # noqa: E731
+    sc_b = dict(sc, grid=rb(sc["grid"]), p_xy=rb(sc["p_xy"]), p_xz=rb(sc["p_xz"]), p_yz=rb(sc["p_yz"]))
+    batch = synth.make_train_batch(5, 4096)
+    scene = gpu_scene(sc)
+    assert scene.feat_dtype == torch.bfloat16
+    res = om.train_step(scene, batch["rays"], batch["target"], batch["smooth_dirs"], lam=LAM)
+    torch.cuda.synchronize()
+    ref = oracle.train(oracle.OracleScene(sc_b), batch["rays"], batch["target"], batch["smooth_dirs"], lam=LAM)
+    _check_grads(res, ref, what="bf16")
