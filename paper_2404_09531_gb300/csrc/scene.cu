@@ -393,7 +393,7 @@ omerf_status omerf_build_brick_table(const float aabb[6], const int32_t grid_res
 
 omerf_status omerf_ray_interval(const omerf_scene* s, const omerf_camera* cam, const float* rays, int64_t n,
                                 int32_t* k_range, void* stream) {
-  if (!s || !k_range) { set_error("NULL argument"); return OMERF_EINVAL; }
+  if (!s || (!k_range && n > 0)) { set_error("NULL argument"); return OMERF_EINVAL; }
   if (n < 0) { set_error("n must be >= 0"); return OMERF_ESHAPE; }
   omerf_status st;
   Cam k{};
@@ -413,7 +413,7 @@ omerf_status omerf_ray_interval(const omerf_scene* s, const omerf_camera* cam, c
 
 omerf_status omerf_render(const omerf_scene* s, const omerf_camera* cam, const float* rays, int64_t n, float* rgb,
                           int32_t* count, void* stream) {
-  if (!s || !rgb) { set_error("NULL argument"); return OMERF_EINVAL; }
+  if (!s || (!rgb && n > 0)) { set_error("NULL argument"); return OMERF_EINVAL; }
   if (n < 0) { set_error("n must be >= 0"); return OMERF_ESHAPE; }
   omerf_status st;
   Cam k{};
