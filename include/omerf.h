@@ -79,11 +79,11 @@ typedef struct {
     float t_thr;               /* early-termination threshold on T (>= 0) */
     float bg[3];               /* background colour added as T_N * bg */
     int32_t n_max;             /* maximum evaluated samples per ray (1..65536) */
-    const void *grid;          /* device: dense grid or brick pool, 16-byte aligned */
+    const void *grid;          /* device: dense grid or brick pool; 32-byte aligned (float32) or 16 (bfloat16) */
     const int32_t *brick_table;/* device: brick table (brick grids only) */
-    const void *plane_xy;      /* device, 16-byte aligned */
-    const void *plane_xz;      /* device, 16-byte aligned */
-    const void *plane_yz;      /* device, 16-byte aligned */
+    const void *plane_xy;      /* device, aligned like grid */
+    const void *plane_xz;      /* device, aligned like grid */
+    const void *plane_yz;      /* device, aligned like grid */
     const float *occ;          /* device: [M][M][2], 8-byte aligned */
     const float *mlp;          /* device: 883 float32 weights (always float32) */
 } omerf_scene_desc;

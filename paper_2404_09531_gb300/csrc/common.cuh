@@ -43,6 +43,9 @@ struct Geo {
   const float2* occ;
   const float* mlp;
   const float* hull;       // device [2]: min z_min, max z_max over non-empty cells
+  const float2* chull;     // device [Mc][Mc]: coarse max-pooled (min z_min, max z_max)
+  int clog2;               // coarse cell = 2^clog2 x 2^clog2 occupancy cells
+  int Mc;                  // coarse cells per axis
 };
 
 struct Cam {
@@ -129,6 +132,52 @@ __device__ __forceinline__ bool lattice_test(const Geo& g, const float o[3], con
   return zb.x < p[2] && p[2] < zb.y;
 }
 
+// Empty-space skipping (Sec. 4.4: max-pooled occupancy planes and box tests).
+// Lane j reports whether lattice window [kb + 32 j, kb + 32 j + 31] (clipped
+// to kh) may hold an evaluated sample: the window's sample positions lie in
+// the bounding box of its two end points (padded far beyond float32
+// rounding); the decision rule's cell index is monotone in x and y, so the
+// cells of those samples lie in the cell range of the padded box, and a
+// sample can pass only if its z meets the max-pooled interval of a coarse
+// cell in that range.  Windows outside the box or missing every interval
+// are culled; the survivors are still tested sample by sample.
+__device__ __forceinline__ unsigned window_mask(const Geo& g, const float o[3], const float d[3], int kb, int kh,
+                                                int lane) {
+  const int ka = kb + 32 * lane;
+  bool maybe = false;
+  if (ka <= kh) {
+    const int kz = min(ka + 31, kh);
+    const float ta = __fmul_rn((float)ka, g.step), tb = __fmul_rn((float)kz, g.step);
+    float lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const float pa = __fadd_rn(o[a], __fmul_rn(ta, d[a])), pb = __fadd_rn(o[a], __fmul_rn(tb, d[a]));
+      const float pad = 1e-5f * (1.0f + fmaxf(fabsf(pa), fabsf(pb)));
+      lo[a] = fminf(pa, pb) - pad;
+      hi[a] = fmaxf(pa, pb) + pad;
+    }
+    const bool in_box = hi[0] >= g.lo[0] && lo[0] <= g.hi[0] && hi[1] >= g.lo[1] && lo[1] <= g.hi[1] &&
+                        hi[2] >= g.lo[2] && lo[2] <= g.hi[2];
+    if (in_box) {
+      const int cx0 = min(max((int)floorf(__fmul_rn(__fsub_rn(fmaxf(lo[0], g.lo[0]), g.lo[0]), g.osx)), 0), g.M - 1);
+      const int cx1 = min(max((int)floorf(__fmul_rn(__fsub_rn(fminf(hi[0], g.hi[0]), g.lo[0]), g.osx)), 0), g.M - 1);
+      const int cy0 = min(max((int)floorf(__fmul_rn(__fsub_rn(fmaxf(lo[1], g.lo[1]), g.lo[1]), g.osy)), 0), g.M - 1);
+      const int cy1 = min(max((int)floorf(__fmul_rn(__fsub_rn(fminf(hi[1], g.hi[1]), g.lo[1]), g.osy)), 0), g.M - 1);
+      const int X0 = cx0 >> g.clog2, X1 = cx1 >> g.clog2, Y0 = cy0 >> g.clog2, Y1 = cy1 >> g.clog2;
+      if ((X1 - X0 + 1) * (Y1 - Y0 + 1) > 16) {
+        maybe = true;  // unusually long window in cell units: keep it
+      } else {
+        for (int X = X0; X <= X1 && !maybe; X++)
+          for (int Y = Y0; Y <= Y1 && !maybe; Y++) {
+            const float2 h = __ldg(g.chull + X * g.Mc + Y);
+            maybe = h.x <= hi[2] && h.y >= lo[2];
+          }
+      }
+    }
+  }
+  return __ballot_sync(kFull, maybe);
+}
+
 // Eq. 6 with q = 2; overlapping ramps take the smaller value.  branch: 0 flat,
 // 1 lower ramp (r = (z - z_min)/eps), 2 upper ramp (r = (z_max - z)/eps).
 __device__ __forceinline__ float occupancy(const Geo& g, float z, float2 zb, int& branch, float& r) {
@@ -158,11 +207,12 @@ struct Texel;
 template <>
 struct Texel<float> {
   static constexpr int kBytes = 32;
+  // one 256-bit read-only load per texel (sm_100+ vector width)
   __device__ __forceinline__ static void load(const void* base, int elem, float v[8]) {
-    const float4* q = reinterpret_cast<const float4*>(static_cast<const float*>(base) + elem);
-    float4 a = __ldg(q), b = __ldg(q + 1);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    const float* q = static_cast<const float*>(base) + elem;
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(q));
   }
 };
 
@@ -276,6 +326,8 @@ __device__ __forceinline__ void gather_features(const Geo& g, const float p[3], 
 }
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+// hardware exp2 based sigmoid for the per-sample activations (relative error ~1e-6)
+__device__ __forceinline__ float sigmoid_fast(float x) { return __frcp_rn(1.0f + __expf(-x)); }
 
 // Eq. 3 and the opacity of Eq. 1 for one evaluated sample.
 struct SampleAct {
@@ -287,12 +339,14 @@ struct SampleAct {
 
 __device__ __forceinline__ void activate(const Geo& g, const float t[8], float z, float2 zb, SampleAct& s) {
   s.Mv = occupancy(g, z, zb, s.branch, s.r);
-  float tau = expf(t[0]);
+  const float tau = __expf(t[0]);
   s.sigma = tau * g.step;
-  s.alpha = -expm1f(-s.sigma);
+  // 1 - exp(-sigma): series for small sigma keeps the relative accuracy of alpha
+  s.alpha = s.sigma < 1e-3f ? s.sigma * (1.0f - 0.5f * s.sigma * (1.0f - s.sigma * (1.0f / 3.0f)))
+                            : 1.0f - __expf(-s.sigma);
   s.ah = s.Mv * s.alpha;
 #pragma unroll
-  for (int c = 0; c < 7; c++) s.x[c] = sigmoidf_(t[c + 1]);
+  for (int c = 0; c < 7; c++) s.x[c] = sigmoid_fast(t[c + 1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -307,6 +361,11 @@ __device__ __forceinline__ float warp_sum(float v) {
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+__device__ __forceinline__ unsigned lanemask_le() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
   return m;
 }
 
@@ -333,6 +392,72 @@ __device__ __forceinline__ void view_encoding(const float d[3], float* x) {
       x[3 + 6 * k + a] = s;
       x[3 + 6 * k + 3 + a] = c;
     }
+  }
+}
+
+// Shared-memory copy of the MLP with 16-byte aligned rows (W1 rows padded to
+// 36) so that every layer is read with 128-bit broadcast loads.
+constexpr int kSW1 = 0, kSB1 = 576, kSW2 = 592, kSB2 = 848, kSW3 = 864, kSB3 = 912, kSmemMlp = 916;
+
+__device__ __forceinline__ void load_mlp_padded(const float* __restrict__ gw, float* __restrict__ sw) {
+  for (int i = threadIdx.x; i < kSmemMlp; i += blockDim.x) {
+    float v = 0.0f;
+    if (i < kSB1) {
+      const int j = i / 36, c = i % 36;
+      v = c < 34 ? gw[kOffW1 + j * 34 + c] : 0.0f;
+    } else if (i < kSW2) {
+      v = gw[kOffB1 + i - kSB1];
+    } else if (i < kSB2) {
+      v = gw[kOffW2 + i - kSW2];
+    } else if (i < kSW3) {
+      v = gw[kOffB2 + i - kSB2];
+    } else if (i < kSB3) {
+      v = gw[kOffW3 + i - kSW3];
+    } else if (i < kSB3 + 3) {
+      v = gw[kOffB3 + i - kSB3];
+    }
+    sw[i] = v;
+  }
+}
+
+__device__ __forceinline__ float dot4(float4 w, float a, float b, float c, float d, float acc) {
+  return fmaf(w.w, d, fmaf(w.z, c, fmaf(w.y, b, fmaf(w.x, a, acc))));
+}
+
+// G(F, d) -> y with the padded shared-memory weights (thread per ray).
+__device__ __forceinline__ void mlp_forward_padded(const float* __restrict__ W, const float F[7], const float d[3],
+                                                   float y[3]) {
+  float x[36];
+#pragma unroll
+  for (int i = 0; i < 7; i++) x[i] = F[i];
+  view_encoding(d, x + 7);
+  x[34] = 0.0f;
+  x[35] = 0.0f;
+  float h1[16];
+#pragma unroll
+  for (int j = 0; j < 16; j++) {
+    const float4* w = reinterpret_cast<const float4*>(W + kSW1 + 36 * j);
+    float a = W[kSB1 + j];
+#pragma unroll
+    for (int q = 0; q < 9; q++) a = dot4(w[q], x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3], a);
+    h1[j] = fmaxf(a, 0.0f);
+  }
+  float h2[16];
+#pragma unroll
+  for (int j = 0; j < 16; j++) {
+    const float4* w = reinterpret_cast<const float4*>(W + kSW2 + 16 * j);
+    float a = W[kSB2 + j];
+#pragma unroll
+    for (int q = 0; q < 4; q++) a = dot4(w[q], h1[4 * q], h1[4 * q + 1], h1[4 * q + 2], h1[4 * q + 3], a);
+    h2[j] = fmaxf(a, 0.0f);
+  }
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    const float4* w = reinterpret_cast<const float4*>(W + kSW3 + 16 * j);
+    float a = W[kSB3 + j];
+#pragma unroll
+    for (int q = 0; q < 4; q++) a = dot4(w[q], h2[4 * q], h2[4 * q + 1], h2[4 * q + 2], h2[4 * q + 3], a);
+    y[j] = sigmoidf_(a);
   }
 }
 

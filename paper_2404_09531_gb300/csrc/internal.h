@@ -11,6 +11,8 @@ struct omerf_scene {
   omerf::Geo geo;
   float* state = nullptr;          // device: [0..1] occupancy hull (min z_min, max z_max)
   unsigned* counters = nullptr;    // device: per-launch work counters
+  float2* chull = nullptr;         // device: coarse max-pooled occupancy grid [Mc][Mc]
+  int clog2 = 0, Mc = 1;
   mutable std::atomic<unsigned> seq{0};
   int device = 0;
   int num_sms = 0;

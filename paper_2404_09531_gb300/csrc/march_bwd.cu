@@ -15,6 +15,7 @@
 //     and Eq. 6 and scatter-adds into the grid, planes and z-bounds with
 //     vector float atomics.  No per-sample state is stored between passes.
 #include "internal.h"
+#include "packed.cuh"
 
 namespace omerf {
 
@@ -166,35 +167,43 @@ __device__ __forceinline__ void scatter8(float* base, int off, float w, const fl
   atomicAdd(q + 1, make_float4(w * dt[4], w * dt[5], w * dt[6], w * dt[7]));
 }
 
+// Per-warp shared state of the packed backward re-march of 32 rays.
+struct WarpBwd {
+  WarpQueue q;
+  float F[32][8];    // per-ray F (7)
+  float G[32][8];    // per-ray dL/dF (7), dL/dT_N
+  float A[32][8];    // per-ray running prefix of w x
+  float T[32];       // per-ray transmittance so far
+  float TN[32];
+  int cnt[32];       // per-ray sample count of the forward
+  int done[32];      // per-ray samples already processed
+};
+
+// Re-march a bundle exactly like the forward (same lattice candidates, same
+// decisions, the first `count` evaluated samples of each ray) and scatter the
+// per-sample gradients.  Lane r owns ray r of the bundle.
 template <class FT, bool SPARSE>
-__device__ __forceinline__ void march_ray_bwd(const Geo& g, const BwdArgs& a, const float o[3], const float d[3],
-                                              int klo, int khi, int count, const float F[7], float TN,
-                                              const float gF[7], float gT, int lane) {
-  float T = 1.0f;
-  float A[7] = {0, 0, 0, 0, 0, 0, 0};
-  int cnt = 0;
-  for (int k = klo; k <= khi && cnt < count; k += 32) {
-    const int kk = k + lane;
-    float p[3];
-    float2 zb = make_float2(0.0f, 0.0f);
-    int cell = 0;
-    bool ok = kk <= khi && lattice_test(g, o, d, kk, p, zb, cell);
-    unsigned m = __ballot_sync(kFull, ok);
-    if (m == 0u) continue;
-    const int room = count - cnt;
-    const int rank = __popc(m & lanemask_lt());
-    if (__popc(m) > room) {
-      if (ok && rank >= room) ok = false;
-      m = __ballot_sync(kFull, ok);
-    }
+__device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a, int lane, const float o[3],
+                                                 const float d[3], int klo, int khi, bool live, WarpBwd& ws) {
+  const int mycnt = ws.cnt[lane];
+  unsigned pend = __ballot_sync(kFull, live);
+  FillState f;
+  while (pend) {
+    const int nq = fill_queue(g, lane, o, d, klo, khi, mycnt, pend, f, ws.q);
+    if (nq == 0) break;
+    const bool act = lane < nq;
+    const float4 qa = ws.q.a[lane], qb = ws.q.b[lane];
+    const int r = act ? __float_as_int(qb.y) : 32;
     SampleAct s;
     s.ah = 0.0f;
     s.alpha = 0.0f;
+    s.branch = 0;
 #pragma unroll
     for (int c = 0; c < 7; c++) s.x[c] = 0.0f;
     int goff[8], poff[12];
     float gw[8], pw[12];
-    if (ok) {
+    if (act) {
+      const float p[3] = {qa.x, qa.y, qa.z};
       grid_stencil<SPARSE>(g, p, goff, gw);
       plane_stencil(g, p, poff, pw);
       float t[8];
@@ -218,48 +227,42 @@ __device__ __forceinline__ void march_ray_bwd(const Geo& g, const BwdArgs& a, co
           for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(pw[4 * q + c], v[ch], t[ch]);
         }
       }
-      activate(g, t, p[2], zb, s);
+      activate(g, t, p[2], make_float2(qa.w, qb.x), s);
     }
-    float P = 1.0f - s.ah;
-#pragma unroll
-    for (int sh = 1; sh < 32; sh <<= 1) {
-      const float v = __shfl_up_sync(kFull, P, sh);
-      if (lane >= sh) P *= v;
-    }
+    bool head;
+    const int segstart = segment_start(lane, r, head);
+    const float P = seg_prod_scan(1.0f - s.ah, lane, segstart);
     float Pex = __shfl_up_sync(kFull, P, 1);
-    if (lane == 0) Pex = 1.0f;
-    const float Ti = T * Pex, Tn = T * P;
-    const float w = ok ? Ti * s.ah : 0.0f;
-    // inclusive lane scan of w * x (prefix of F)
+    if (head) Pex = 1.0f;
+    const float Tprev = act ? ws.T[r] : 1.0f;
+    const float Ti = Tprev * Pex, Tn = Tprev * P;
+    const float w = act ? Ti * s.ah : 0.0f;
     float Ai[7];
 #pragma unroll
-    for (int c = 0; c < 7; c++) {
-      float v = w * s.x[c];
-#pragma unroll
-      for (int sh = 1; sh < 32; sh <<= 1) {
-        const float u = __shfl_up_sync(kFull, v, sh);
-        if (lane >= sh) v += u;
-      }
-      Ai[c] = A[c] + v;
-    }
-    if (ok) {
+    for (int c = 0; c < 7; c++) Ai[c] = w * s.x[c];
+    seg_sum_scan7(Ai, lane, segstart);
+    if (act) {
+      const int idx = ws.done[r] + (lane - segstart);
+      const bool last = idx == ws.cnt[r] - 1;
+      const float gT = ws.G[r][7], TN = ws.TN[r];
       float gx = 0.0f, suffix = gT * TN;
 #pragma unroll
       for (int c = 0; c < 7; c++) {
-        gx = fmaf(gF[c], s.x[c], gx);
-        suffix = fmaf(gF[c], F[c] - Ai[c], suffix);
+        Ai[c] += ws.A[r][c];
+        const float gc = ws.G[r][c];
+        gx = fmaf(gc, s.x[c], gx);
+        suffix = fmaf(gc, ws.F[r][c] - Ai[c], suffix);
       }
-      const bool last = (cnt + rank) == count - 1;
       const float dah = last ? Ti * (gx - gT) : Ti * gx - suffix / (1.0f - s.ah);
       const float dsig = dah * s.Mv * (1.0f - s.alpha);
       float dt[8];
       dt[0] = dsig * s.sigma;
 #pragma unroll
-      for (int c = 0; c < 7; c++) dt[c + 1] = w * gF[c] * s.x[c] * (1.0f - s.x[c]);
+      for (int c = 0; c < 7; c++) dt[c + 1] = w * ws.G[r][c] * s.x[c] * (1.0f - s.x[c]);
       if (a.g_occ && s.branch != 0) {
         const float dM = dah * s.alpha;
         const float dz = (s.branch == 1 ? -2.0f : 2.0f) * s.r * g.inv_eps;
-        atomicAdd(a.g_occ + 2 * cell + (s.branch == 1 ? 0 : 1), dM * dz);
+        atomicAdd(a.g_occ + 2 * __float_as_int(qb.z) + (s.branch == 1 ? 0 : 1), dM * dz);
       }
       if (a.g_grid) {
 #pragma unroll
@@ -274,11 +277,16 @@ __device__ __forceinline__ void march_ray_bwd(const Geo& g, const BwdArgs& a, co
         for (int c = 0; c < 4; c++) scatter8(gp[q], poff[4 * q + c], pw[4 * q + c], dt);
       }
     }
-    const int lastlane = 31 - __clz(m);
-    T = __shfl_sync(kFull, Tn, lastlane);
+    const int rnext = __shfl_down_sync(kFull, r, 1);
+    const bool tail = act && (lane == 31 || rnext != r);
+    __syncwarp();
+    if (tail) {
 #pragma unroll
-    for (int c = 0; c < 7; c++) A[c] = __shfl_sync(kFull, Ai[c], lastlane);
-    cnt += __popc(m);
+      for (int c = 0; c < 7; c++) ws.A[r][c] = Ai[c];
+      ws.T[r] = Tn;
+      ws.done[r] += lane - segstart + 1;
+    }
+    __syncwarp();
   }
 }
 
@@ -381,9 +389,15 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
 
 // Kernel 2: re-march every ray (one warp per bundle of 32 rays, persistent)
 // and scatter the per-sample gradients.
+#ifndef OMERF_BWD_MINB
+#define OMERF_BWD_MINB 2  // resident CTAs per SM the register budget is sized for
+#endif
+
 template <class FT, bool SPARSE>
-__global__ void __launch_bounds__(kThreads) march_bwd_kernel(const Geo g, const BwdArgs a) {
+__global__ void __launch_bounds__(kThreads, OMERF_BWD_MINB) march_bwd_kernel(const Geo g, const BwdArgs a) {
+  __shared__ WarpBwd sBwd[kThreads / 32];
   const int lane = threadIdx.x & 31;
+  WarpBwd& ws = sBwd[threadIdx.x >> 5];
   for (;;) {
     unsigned b = 0;
     if (lane == 0) b = atomicAdd(a.counter, 1u);
@@ -392,37 +406,32 @@ __global__ void __launch_bounds__(kThreads) march_bwd_kernel(const Geo g, const 
     const long rid = (long)b * 32 + lane;
     const bool valid = rid < a.n;
     float o[3] = {0, 0, 0}, d[3] = {0, 0, 1};
-    int cnt = 0;
+    int cnt = 0, klo = 0, khi = -1;
     if (valid) {
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         o[c] = __ldg(a.rays + 6 * rid + c);
         d[c] = __ldg(a.rays + 6 * rid + 3 + c);
       }
-      cnt = __float_as_int(__ldg(a.saved + (long)kSavedFloats * rid + 8));
+      const float4* sv = reinterpret_cast<const float4*>(a.saved + (long)kSavedFloats * rid);
+      const float4 s0 = __ldg(sv), s1 = __ldg(sv + 1), s2 = __ldg(sv + 2), s3 = __ldg(sv + 3),
+                   s4 = __ldg(sv + 4);
+      ws.F[lane][0] = s0.x; ws.F[lane][1] = s0.y; ws.F[lane][2] = s0.z; ws.F[lane][3] = s0.w;
+      ws.F[lane][4] = s1.x; ws.F[lane][5] = s1.y; ws.F[lane][6] = s1.z; ws.TN[lane] = s1.w;
+      cnt = __float_as_int(s2.x);
+      klo = __float_as_int(s2.y);
+      khi = __float_as_int(s2.z);
+      ws.G[lane][0] = s3.x; ws.G[lane][1] = s3.y; ws.G[lane][2] = s3.z; ws.G[lane][3] = s3.w;
+      ws.G[lane][4] = s4.x; ws.G[lane][5] = s4.y; ws.G[lane][6] = s4.z; ws.G[lane][7] = s4.w;
     }
-    unsigned todo = __ballot_sync(kFull, valid && cnt > 0);
-    while (todo) {
-      const int r = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const long rr = b * 32l + r;
-      const float* sv = a.saved + (long)kSavedFloats * rr;
-      float ro[3], rd[3], rF[7], rg[7];
+    ws.cnt[lane] = cnt;
+    ws.done[lane] = 0;
+    ws.T[lane] = 1.0f;
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        ro[c] = __shfl_sync(kFull, o[c], r);
-        rd[c] = __shfl_sync(kFull, d[c], r);
-      }
-#pragma unroll
-      for (int c = 0; c < 7; c++) {
-        rF[c] = __ldg(sv + c);
-        rg[c] = __ldg(sv + 12 + c);
-      }
-      const float rTN = __ldg(sv + 7), rgT = __ldg(sv + 19);
-      const int rcnt = __float_as_int(__ldg(sv + 8));
-      const int rklo = __float_as_int(__ldg(sv + 9)), rkhi = __float_as_int(__ldg(sv + 10));
-      march_ray_bwd<FT, SPARSE>(g, a, ro, rd, rklo, rkhi, rcnt, rF, rTN, rg, rgT, lane);
-    }
+    for (int c = 0; c < 8; c++) ws.A[lane][c] = 0.0f;
+    __syncwarp();
+    march_bundle_bwd<FT, SPARSE>(g, a, lane, o, d, klo, khi, valid && cnt > 0, ws);
+    __syncwarp();
   }
 }
 

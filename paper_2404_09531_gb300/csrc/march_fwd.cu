@@ -12,59 +12,87 @@
 #include <cstdio>
 
 #include "internal.h"
+#include "packed.cuh"
 
 namespace omerf {
 
-// March one ray with the whole warp.  acc receives this lane's share of
-// F = [sum w c^d, sum w f]; T and cnt are warp-uniform on return.
+// Per-warp shared state of the packed march of one bundle of 32 rays.
+struct WarpMarch {
+  WarpQueue q;
+  float F[32][8];    // per-ray accumulated [sum w c^d, sum w f]
+  float T[32];       // per-ray transmittance so far
+  int cnt[32];       // per-ray evaluated samples
+};
+
+// March the 32 rays of a bundle (lane r owns ray r: o, d, [klo, khi]).
+//
+// fill:    evaluated samples of consecutive rays are queued, 32 at a time
+//          (packed.cuh);
+// process: the 32 queued samples are gathered and activated in parallel;
+//          compositing is a segmented lane scan (segments = rays) of
+//          1 - alpha_hat, early termination is resolved per segment, and
+//          the weighted features are summed per segment into the ray's
+//          accumulator.
+// On return ws.F / ws.T / ws.cnt hold every ray's F, T_N and sample count.
 template <class FT, bool SPARSE>
-__device__ __forceinline__ void march_ray(const Geo& g, const float o[3], const float d[3], int klo, int khi,
-                                          int lane, float acc[7], float& T, int& cnt) {
-  T = 1.0f;
-  cnt = 0;
-  for (int k = klo; k <= khi; k += 32) {
-    const int kk = k + lane;
-    float p[3];
-    float2 zb = make_float2(0.0f, 0.0f);
-    int cell = 0;
-    bool ok = kk <= khi && lattice_test(g, o, d, kk, p, zb, cell);
-    unsigned m = __ballot_sync(kFull, ok);
-    if (m == 0u) continue;
-    const int room = g.n_max - cnt;
-    if (__popc(m) > room) {
-      if (ok && __popc(m & lanemask_lt()) >= room) ok = false;
-      m = __ballot_sync(kFull, ok);
-    }
+__device__ __forceinline__ void march_bundle(const Geo& g, int lane, const float o[3], const float d[3], int klo,
+                                             int khi, bool any, WarpMarch& ws) {
+#pragma unroll
+  for (int c = 0; c < 8; c++) ws.F[lane][c] = 0.0f;
+  ws.T[lane] = 1.0f;
+  ws.cnt[lane] = 0;
+  unsigned pend = __ballot_sync(kFull, any);
+  FillState f;
+  __syncwarp();
+  while (pend) {
+    const int nq = fill_queue(g, lane, o, d, klo, khi, g.n_max, pend, f, ws.q);
+    if (nq == 0) break;
+    const bool act = lane < nq;
+    const float4 qa = ws.q.a[lane], qb = ws.q.b[lane];
+    const int r = act ? __float_as_int(qb.y) : 32;
     SampleAct s;
     s.ah = 0.0f;
-    if (ok) {
+#pragma unroll
+    for (int c = 0; c < 7; c++) s.x[c] = 0.0f;
+    if (act) {
+      const float p[3] = {qa.x, qa.y, qa.z};
       float t[8];
       gather_features<FT, SPARSE>(g, p, t);
-      activate(g, t, p[2], zb, s);
+      activate(g, t, p[2], make_float2(qa.w, qb.x), s);
     }
-    // transmittance: inclusive product scan of (1 - alpha_hat) over the lanes
-    float P = 1.0f - s.ah;
-#pragma unroll
-    for (int sh = 1; sh < 32; sh <<= 1) {
-      float v = __shfl_up_sync(kFull, P, sh);
-      if (lane >= sh) P *= v;
-    }
+    bool head;
+    const int segstart = segment_start(lane, r, head);
+    // transmittance: segmented inclusive product scan of (1 - alpha_hat)
+    const float P = seg_prod_scan(1.0f - s.ah, lane, segstart);
     float Pex = __shfl_up_sync(kFull, P, 1);
-    if (lane == 0) Pex = 1.0f;
-    const float Ti = T * Pex, Tn = T * P;
-    const unsigned tm = __ballot_sync(kFull, ok && Tn < g.t_thr);
-    if (tm) {
-      if (lane > __ffs(tm) - 1) ok = false;
-      m = __ballot_sync(kFull, ok);
-    }
-    if (ok) {
-      const float w = Ti * s.ah;
+    if (head) Pex = 1.0f;
+    const float Tprev = act ? ws.T[r] : 1.0f;
+    const float Ti = Tprev * Pex, Tn = Tprev * P;
+    // early termination: the first sample of a segment whose T drops below t_thr ends the ray
+    const bool term = act && Tn < g.t_thr;
+    const unsigned tm = __ballot_sync(kFull, term);
+    const unsigned seglt = lanemask_lt() & ~((1u << segstart) - 1u);
+    const bool dropped = (tm & seglt) != 0u;
+    const bool ok = act && !dropped;
+    const float w = ok ? Ti * s.ah : 0.0f;
+    float wx[7];
 #pragma unroll
-      for (int c = 0; c < 7; c++) acc[c] = fmaf(w, s.x[c], acc[c]);
+    for (int c = 0; c < 7; c++) wx[c] = w * s.x[c];
+    seg_sum_scan7(wx, lane, segstart);
+    const unsigned okm = __ballot_sync(kFull, ok);
+    const int rnext = __shfl_down_sync(kFull, r, 1);
+    const bool tail = act && (lane == 31 || rnext != r);
+    const unsigned segle = lanemask_le() & ~((1u << segstart) - 1u);
+    if (tail) {
+#pragma unroll
+      for (int c = 0; c < 7; c++) ws.F[r][c] += wx[c];
+      ws.cnt[r] += __popc(okm & segle);
+      if (!(tm & segle)) ws.T[r] = Tn;
     }
-    T = __shfl_sync(kFull, Tn, 31 - __clz(m));
-    cnt += __popc(m);
-    if (tm || cnt >= g.n_max) break;
+    const bool first_term = term && !dropped;
+    if (first_term) ws.T[r] = Tn;
+    pend &= ~__reduce_or_sync(kFull, first_term ? (1u << r) : 0u);
+    __syncwarp();
   }
 }
 
@@ -85,13 +113,19 @@ struct FwdArgs {
   unsigned* counter;
 };
 
+#ifndef OMERF_FWD_MINB
+#define OMERF_FWD_MINB 3  // resident CTAs per SM the register budget is sized for
+#endif
+
 template <class FT, bool SPARSE, bool TRAIN>
-__global__ void __launch_bounds__(kThreads) march_fwd_kernel(const Geo g, const FwdArgs a) {
-  __shared__ float sW[kMlpParams];
+__global__ void __launch_bounds__(kThreads, OMERF_FWD_MINB) march_fwd_kernel(const Geo g, const FwdArgs a) {
+  __shared__ __align__(16) float sW[kSmemMlp];
   __shared__ float sLoss[2][kThreads / 32];
-  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sW[i] = g.mlp[i];
+  __shared__ WarpMarch sMarch[kThreads / 32];
+  load_mlp_padded(g.mlp, sW);
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  WarpMarch& ws = sMarch[threadIdx.x >> 5];
   float l_rgb = 0.0f, l_smooth = 0.0f;
 
   for (;;) {
@@ -123,35 +157,13 @@ __global__ void __launch_bounds__(kThreads) march_fwd_kernel(const Geo g, const 
     }
     int klo = 0, khi = -1;
     const bool any = valid && lattice_range(g, o, d, klo, khi);
-
-    float F[7] = {0, 0, 0, 0, 0, 0, 0};
-    float T = 1.0f;
-    int cnt = 0;
-    unsigned todo = __ballot_sync(kFull, any);
-    while (todo) {
-      const int r = __ffs(todo) - 1;
-      todo &= todo - 1;
-      float ro[3], rd[3];
+    march_bundle<FT, SPARSE>(g, lane, o, d, klo, khi, any, ws);
+    float F[7];
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        ro[c] = __shfl_sync(kFull, o[c], r);
-        rd[c] = __shfl_sync(kFull, d[c], r);
-      }
-      const int rklo = __shfl_sync(kFull, klo, r), rkhi = __shfl_sync(kFull, khi, r);
-      float acc[7] = {0, 0, 0, 0, 0, 0, 0};
-      float rT;
-      int rc;
-      march_ray<FT, SPARSE>(g, ro, rd, rklo, rkhi, lane, acc, rT, rc);
-#pragma unroll
-      for (int c = 0; c < 7; c++) {
-        const float v = warp_sum(acc[c]);
-        if (lane == r) F[c] = v;
-      }
-      if (lane == r) {
-        T = rT;
-        cnt = rc;
-      }
-    }
+    for (int c = 0; c < 7; c++) F[c] = ws.F[lane][c];
+    const float T = ws.T[lane];
+    const int cnt = ws.cnt[lane];
+    __syncwarp();
 
     if (valid) {
       float out[3], yd[3] = {0.0f, 0.0f, 0.0f};
@@ -159,13 +171,9 @@ __global__ void __launch_bounds__(kThreads) march_fwd_kernel(const Geo g, const 
 #pragma unroll
         for (int j = 0; j < 3; j++) out[j] = g.bg[j];
       } else {
-        MlpCache mc;
-        mlp_forward(sW, F, d, mc);
+        mlp_forward_padded(sW, F, d, yd);
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-          yd[j] = mc.y[j];
-          out[j] = F[j] + mc.y[j] + T * g.bg[j];
-        }
+        for (int j = 0; j < 3; j++) out[j] = F[j] + yd[j] + T * g.bg[j];
       }
       if (!TRAIN) {
 #pragma unroll
@@ -187,11 +195,11 @@ __global__ void __launch_bounds__(kThreads) march_fwd_kernel(const Geo g, const 
             const float sn = sqrtf(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
             const float S = (d[0] * sv[0] + d[1] * sv[1] + d[2] * sv[2]) / (dn * sn);
             float sh[3] = {sv[0] / sn, sv[1] / sn, sv[2] / sn};
-            MlpCache ms;
-            mlp_forward(sW, F, sh, ms);
+            float ys[3];
+            mlp_forward_padded(sW, F, sh, ys);
             float q = 0.0f;
 #pragma unroll
-            for (int j = 0; j < 3; j++) q = fmaf(ms.y[j] - yd[j], ms.y[j] - yd[j], q);
+            for (int j = 0; j < 3; j++) q = fmaf(ys[j] - yd[j], ys[j] - yd[j], q);
             l_smooth = fmaf(S, q, l_smooth);
           }
         }

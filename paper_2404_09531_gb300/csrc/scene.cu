@@ -61,6 +61,27 @@ __global__ void hull_kernel(const float2* __restrict__ occ, long cells, float* _
   }
 }
 
+// Coarse max-pooled occupancy grid (Sec. 4.4: 2D max pooling of the occupancy
+// plane for empty-space skipping): cell (X, Y) holds the min z_min and max
+// z_max over the non-empty occupancy cells it covers, (+inf, -inf) if none.
+__global__ void coarse_hull_kernel(const float2* __restrict__ occ, int M, int clog2, int Mc,
+                                   float2* __restrict__ chull) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= Mc * Mc) return;
+  const int X = id / Mc, Y = id % Mc;
+  float lo = __int_as_float(0x7f800000), hi = -lo;
+  const int i1 = min((X + 1) << clog2, M), j1 = min((Y + 1) << clog2, M);
+  for (int i = X << clog2; i < i1; i++)
+    for (int j = Y << clog2; j < j1; j++) {
+      const float2 z = occ[i * M + j];
+      if (z.x <= z.y) {
+        lo = fminf(lo, z.x);
+        hi = fmaxf(hi, z.y);
+      }
+    }
+  chull[id] = make_float2(lo, hi);
+}
+
 // ---------------------------------------------------------------------------
 // brick allocation (Sec. 4.4)
 // ---------------------------------------------------------------------------
@@ -229,8 +250,10 @@ static omerf_status validate_desc(const omerf_scene_desc* d) {
     set_error("a scene array pointer is NULL");
     return OMERF_EINVAL;
   }
-  if (!aligned(d->grid, 16) || !aligned(d->plane_xy, 16) || !aligned(d->plane_xz, 16) || !aligned(d->plane_yz, 16)) {
-    set_error("feature arrays must be 16-byte aligned");
+  // one texel (8 channels) is read with a single 256-bit (float32) or 128-bit (bfloat16) load
+  const size_t fa = d->feat_dtype == OMERF_F32 ? 32 : 16;
+  if (!aligned(d->grid, fa) || !aligned(d->plane_xy, fa) || !aligned(d->plane_xz, fa) || !aligned(d->plane_yz, fa)) {
+    set_error("feature arrays must be %zu-byte aligned", fa);
     return OMERF_EINVAL;
   }
   if (!aligned(d->occ, 8) || !aligned(d->mlp, 4)) { set_error("occ must be 8-byte aligned"); return OMERF_EINVAL; }
@@ -288,6 +311,21 @@ static void fill_geo(omerf_scene* s) {
   g.occ = reinterpret_cast<const float2*>(d.occ);
   g.mlp = d.mlp;
   g.hull = s->state;
+  g.chull = s->chull;
+  g.clog2 = s->clog2;
+  g.Mc = s->Mc;
+}
+
+// Coarse level: the smallest power-of-two block of occupancy cells whose side
+// is at least one 32-sample lattice window, so a window meets at most a few
+// coarse cells.
+static void choose_coarse_level(omerf_scene* s) {
+  const omerf_scene_desc& d = s->desc;
+  const float cw = std::min((d.aabb[1] - d.aabb[0]) / d.occ_res, (d.aabb[3] - d.aabb[2]) / d.occ_res);
+  int l = 0;
+  while (l < 20 && cw * (float)(1 << l) < 32.0f * d.step && (1 << l) < d.occ_res) l++;
+  s->clog2 = l;
+  s->Mc = (d.occ_res + (1 << l) - 1) >> l;
 }
 
 static omerf_status validate_camera(const omerf_camera* c, int64_t n) {
@@ -339,6 +377,16 @@ omerf_status omerf_scene_create(const omerf_scene_desc* desc, void* stream, omer
   if (e != cudaSuccess) { cudaGetLastError(); delete s; set_error("cudaMalloc: %s", cudaGetErrorString(e)); return OMERF_ENOMEM; }
   e = cudaMalloc(&s->counters, kCounterSlots * sizeof(unsigned));
   if (e != cudaSuccess) { cudaGetLastError(); cudaFree(s->state); delete s; set_error("cudaMalloc: %s", cudaGetErrorString(e)); return OMERF_ENOMEM; }
+  choose_coarse_level(s);
+  e = cudaMalloc(&s->chull, (size_t)s->Mc * s->Mc * sizeof(float2));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(s->state);
+    cudaFree(s->counters);
+    delete s;
+    set_error("cudaMalloc: %s", cudaGetErrorString(e));
+    return OMERF_ENOMEM;
+  }
   fill_geo(s);
   st = omerf_scene_update(s, stream);
   if (st != OMERF_OK) { omerf_scene_destroy(s); return st; }
@@ -350,6 +398,9 @@ omerf_status omerf_scene_update(omerf_scene* s, void* stream) {
   if (!s) { set_error("scene is NULL"); return OMERF_EINVAL; }
   const long cells = (long)s->desc.occ_res * s->desc.occ_res;
   hull_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(s->geo.occ, cells, s->state);
+  const int nc = s->Mc * s->Mc;
+  coarse_hull_kernel<<<(nc + 255) / 256, 256, 0, (cudaStream_t)stream>>>(s->geo.occ, s->desc.occ_res, s->clog2,
+                                                                         s->Mc, s->chull);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "hull kernel");
 }
@@ -358,6 +409,7 @@ void omerf_scene_destroy(omerf_scene* s) {
   if (!s) return;
   cudaFree(s->state);
   cudaFree(s->counters);
+  cudaFree(s->chull);
   delete s;
 }
 

@@ -38,14 +38,16 @@ def test_config1_camera_matches_oracle():
 
 
 def test_camera_rays_are_the_oracle_rays():
-    """Rays generated in the kernel give the same counts as the same rays passed in."""
+    """Rays generated in the kernel give the same sample counts as the oracle's
+    pinhole rays passed in as a list (bit-exact), and the same colours up to
+    the summation order of the per-warp batches."""
     sc = synth.make_scene(1)
     scene = gpu_scene(sc)
     cam = synth.make_cameras(1)[0]
     a = _render_np(scene, camera=cam)
     b = _render_np(scene, rays=oracle.camera_rays(cam))
     np.testing.assert_array_equal(a[1], b[1])
-    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_allclose(a[0], b[0], rtol=0, atol=1e-6)
 
 
 @pytest.mark.parametrize("n", [1, 31, 33, 1000, 4097])
