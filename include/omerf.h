@@ -154,6 +154,28 @@ omerf_status omerf_ray_interval(const omerf_scene *scene, const omerf_camera *ca
 omerf_status omerf_render(const omerf_scene *scene, const omerf_camera *cam, const float *rays,
                           int64_t n, float *rgb, int32_t *count, void *stream);
 
+/* Render without allocating (the paper has no counterpart: this is a
+ * deployment variant of omerf_render).  For callers that must not allocate
+ * device memory -- a host framework that owns all device memory and passes in
+ * fixed buffers, or a frame loop that cannot afford cudaMalloc, which may
+ * synchronise the device.  It takes the scene description directly (no
+ * handle) and keeps its scratch (work counters, occupancy hulls) in a 1 MiB
+ * static __device__ array that every GPU loading this library holds until
+ * the process exits.  Arguments, layouts and results are those of
+ * omerf_render.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Occupancy planes whose coarse grid does not fit the array are rejected
+ *     with OMERF_ESHAPE (the coarse grid has ceil(M / 2^l)^2 cells of 8 bytes,
+ *     l the smallest level whose cells span a 32-sample lattice window; about
+ *     130,000 cells fit).
+ *   - Every call reuses the same array: calls whose kernels overlap on the GPU
+ *     (different streams, or several host threads) race and give wrong
+ *     results.  Order them on one stream.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine. */
+omerf_status omerf_render_noalloc(const omerf_scene_desc *desc, const omerf_camera *cam, const float *rays,
+                                  int64_t n, float *rgb, int32_t *count, void *stream);
+
 /* Bytes of per-ray state that omerf_train_fwd writes for omerf_train_bwd. */
 int64_t omerf_saved_bytes_per_ray(void);
 

@@ -14,6 +14,7 @@ from .binding import (  # noqa: F401
     lib,
     ray_interval,
     render,
+    render_noalloc,
     saved_bytes_per_ray,
     scene_from_synth,
     sync,
@@ -23,6 +24,6 @@ from .binding import (  # noqa: F401
 )
 
 __all__ = [
-    "OmerfError", "Scene", "TrainStep", "build_brick_table", "camera_struct", "lib", "ray_interval", "render",
+    "OmerfError", "Scene", "TrainStep", "build_brick_table", "camera_struct", "lib", "ray_interval", "render", "render_noalloc",
     "saved_bytes_per_ray", "scene_from_synth", "sync", "train_bwd", "train_fwd", "train_step",
 ]

@@ -67,6 +67,7 @@ SIGNATURES = {
     "omerf_build_brick_table": (ctypes.c_int, [_P, _P, _I, _P, _I, _P, _P, _P]),
     "omerf_ray_interval": (ctypes.c_int, [_P, _P, _P, _L, _P, _P]),
     "omerf_render": (ctypes.c_int, [_P, _P, _P, _L, _P, _P, _P]),
+    "omerf_render_noalloc": (ctypes.c_int, [_P, _P, _P, _L, _P, _P, _P]),
     "omerf_saved_bytes_per_ray": (ctypes.c_int64, []),
     "omerf_train_fwd": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P]),
     "omerf_train_bwd": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -291,6 +292,31 @@ def render(scene: Scene, camera=None, rays=None, out=None, count_out=None, strea
         if count_out is not None:
             count_out.copy_(count, non_blocking=True)
         return out, count_out
+    return rgb, count
+
+
+def render_noalloc(scene: Scene, camera=None, rays=None, rgb=None, count=None, stream=None):
+    """Render through omerf_render_noalloc, which allocates no device memory.
+
+    For callers that must not allocate: pass preallocated ``rgb`` [n, 3]
+    float32 and ``count`` [n] int32 device tensors (allocated here only when
+    omitted).  The scene's description is used directly; its handle is not.
+    Calls that overlap on the GPU share one static scratch array and race.
+    """
+    dev = scene.device
+    cam_p = None
+    if camera is not None:
+        cs = camera_struct(camera)
+        n = cs.width * cs.height
+        cam_p = ctypes.byref(cs)
+        rays_t = None
+    else:
+        rays_t = _dev_f32(rays, dev)
+        n = int(rays_t.shape[0])
+    if rgb is None:
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    _check(lib().omerf_render_noalloc(ctypes.byref(scene._desc), cam_p, _ptr(rays_t), n, _ptr(rgb), _ptr(count),
+                                      _stream(stream)), "omerf_render_noalloc")
     return rgb, count
 
 

@@ -40,3 +40,17 @@ cudaError_t launch_march_bwd(const omerf_scene* s, const float* rays, const floa
 int persistent_blocks(const void* kernel, int threads, size_t smem, int num_sms);
 
 }  // namespace omerf
+
+// Host helpers shared by the entry points (scene.cu).
+bool aligned(const void* p, size_t a);
+omerf_status cuda_fail(cudaError_t e, const char* what);
+omerf_status validate_desc(const omerf_scene_desc* d);
+void fill_geo(omerf_scene* s);
+void choose_coarse_level(omerf_scene* s);
+omerf_status validate_camera(const omerf_camera* c, int64_t n);
+omerf::Cam to_cam(const omerf_camera* c);
+
+namespace omerf {
+__global__ void hull_kernel(const float2* __restrict__ occ, long cells, float* __restrict__ hull);
+__global__ void coarse_hull_kernel(const float2* __restrict__ occ, int M, int clog2, int Mc, float2* __restrict__ chull);
+}  // namespace omerf

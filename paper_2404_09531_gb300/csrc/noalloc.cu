@@ -1,0 +1,117 @@
+// noalloc.cu -- render entry point that allocates no memory.
+//
+// omerf_render creates nothing per call, but its scene handle owns device
+// state that omerf_scene_create obtains with cudaMalloc: the work counters
+// of the persistent march kernel and the occupancy hulls used for
+// empty-space skipping.  Some callers cannot allocate: a host framework that
+// owns all device memory and hands the renderer fixed buffers, or a frame
+// loop that must never call cudaMalloc (it can synchronise the device and
+// stall the frame).  omerf_render_noalloc renders from a scene description
+// alone; its scratch memory is a file-scope __device__ array that every GPU
+// loading this library holds until the process exits.
+#include <mutex>
+
+#include "internal.h"
+
+namespace omerf {
+
+// Scratch layout: work counters | occupancy hull (2 floats) | coarse grid.
+constexpr size_t kNoAllocCounterBytes = kCounterSlots * sizeof(unsigned);
+constexpr size_t kNoAllocHullOffset = kNoAllocCounterBytes;
+constexpr size_t kNoAllocCoarseOffset = kNoAllocHullOffset + 256;
+constexpr size_t kNoAllocScratchBytes = 1u << 20;  // 1 MiB
+constexpr size_t kNoAllocCoarseMaxCells = (kNoAllocScratchBytes - kNoAllocCoarseOffset) / sizeof(float2);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of the scratch array, looked up once per device (with that
+// device current) by the first call made on it.
+constexpr int kMaxDevices = 64;
+static void* g_scratch_addr[kMaxDevices] = {nullptr};
+static std::mutex g_scratch_mutex;
+
+static omerf_status scratch_address(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal %d is out of range for the no-allocation render", dev);
+    return OMERF_EDEVICE;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      set_error("cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
+      return OMERF_ECUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  return OMERF_OK;
+}
+
+}  // namespace omerf
+
+using namespace omerf;
+
+extern "C" omerf_status omerf_render_noalloc(const omerf_scene_desc* desc, const omerf_camera* cam, const float* rays,
+                                             int64_t n, float* rgb, int32_t* count, void* stream) {
+  omerf_status st = validate_desc(desc);
+  if (st != OMERF_OK) return st;
+  if (!rgb && n > 0) {
+    set_error("rgb is NULL");
+    return OMERF_EINVAL;
+  }
+  if (n < 0) {
+    set_error("n must be >= 0");
+    return OMERF_ESHAPE;
+  }
+  Cam k{};
+  if (cam) {
+    if ((st = validate_camera(cam, n)) != OMERF_OK) return st;
+    k = to_cam(cam);
+  } else if (!rays && n > 0) {
+    set_error("rays is NULL and no camera given");
+    return OMERF_EINVAL;
+  }
+  // A scene on the stack: the same description and geometry as a handle,
+  // with its device state placed in the static scratch array.
+  omerf_scene s;
+  s.desc = *desc;
+  choose_coarse_level(&s);
+  const size_t cells = (size_t)s.Mc * (size_t)s.Mc;
+  if (cells > kNoAllocCoarseMaxCells) {
+    set_error("occupancy plane of %d x %d cells needs a %d x %d coarse grid (%zu bytes), more than the %zu bytes the "
+              "no-allocation render reserves for it",
+              desc->occ_res, desc->occ_res, s.Mc, s.Mc, cells * sizeof(float2),
+              kNoAllocCoarseMaxCells * sizeof(float2));
+    return OMERF_ESHAPE;
+  }
+  cudaError_t e = cudaGetDevice(&s.device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("no CUDA device: %s", cudaGetErrorString(e));
+    return OMERF_EDEVICE;
+  }
+  unsigned char* scratch = nullptr;
+  if ((st = scratch_address(s.device, &scratch)) != OMERF_OK) return st;
+  cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, s.device);
+  if (s.num_sms < 1) s.num_sms = 1;
+  s.counters = reinterpret_cast<unsigned*>(scratch);
+  s.state = reinterpret_cast<float*>(scratch + kNoAllocHullOffset);
+  s.chull = reinterpret_cast<float2*>(scratch + kNoAllocCoarseOffset);
+  fill_geo(&s);
+  if (n == 0) return OMERF_OK;
+  // Every call rebuilds the hulls: the array keeps whatever the previous
+  // call (of any scene) left in it.  The work counter is zeroed by the launch.
+  cudaStream_t cs = (cudaStream_t)stream;
+  const long occ_cells = (long)desc->occ_res * desc->occ_res;
+  hull_kernel<<<1, 1024, 0, cs>>>(s.geo.occ, occ_cells, s.state);
+  coarse_hull_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, cs>>>(s.geo.occ, desc->occ_res, s.clog2, s.Mc,
+                                                                      s.chull);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "no-allocation hull kernels");
+  e = launch_march_fwd(&s, cam ? &k : nullptr, rays, n, rgb, count, nullptr, nullptr, 0, nullptr, nullptr, nullptr,
+                       cs);
+  return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "no-allocation render launch");
+}

@@ -214,14 +214,14 @@ static bool is_pow2_float(float x) {
   return std::frexp(x, &e) == 0.5f;
 }
 
-static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-static omerf_status cuda_fail(cudaError_t e, const char* what) {
+omerf_status cuda_fail(cudaError_t e, const char* what) {
   set_error("%s: %s", what, cudaGetErrorString(e));
   return OMERF_ECUDA;
 }
 
-static omerf_status validate_desc(const omerf_scene_desc* d) {
+omerf_status validate_desc(const omerf_scene_desc* d) {
   if (!d) { set_error("scene description is NULL"); return OMERF_EINVAL; }
   for (int a = 0; a < 3; a++) {
     if (!(d->aabb[2 * a] < d->aabb[2 * a + 1]) || !std::isfinite(d->aabb[2 * a]) || !std::isfinite(d->aabb[2 * a + 1])) {
@@ -276,7 +276,7 @@ static omerf_status check_device_ptr(const void* p, const char* name) {
   return OMERF_OK;
 }
 
-static void fill_geo(omerf_scene* s) {
+void fill_geo(omerf_scene* s) {
   const omerf_scene_desc& d = s->desc;
   Geo& g = s->geo;
   for (int a = 0; a < 3; a++) {
@@ -319,7 +319,7 @@ static void fill_geo(omerf_scene* s) {
 // Coarse level: the smallest power-of-two block of occupancy cells whose side
 // is at least one 32-sample lattice window, so a window meets at most a few
 // coarse cells.
-static void choose_coarse_level(omerf_scene* s) {
+void choose_coarse_level(omerf_scene* s) {
   const omerf_scene_desc& d = s->desc;
   const float cw = std::min((d.aabb[1] - d.aabb[0]) / d.occ_res, (d.aabb[3] - d.aabb[2]) / d.occ_res);
   int l = 0;
@@ -328,7 +328,7 @@ static void choose_coarse_level(omerf_scene* s) {
   s->Mc = (d.occ_res + (1 << l) - 1) >> l;
 }
 
-static omerf_status validate_camera(const omerf_camera* c, int64_t n) {
+omerf_status validate_camera(const omerf_camera* c, int64_t n) {
   if (c->width < 1 || c->height < 1 || (int64_t)c->width * c->height != n) {
     set_error("camera size %d x %d does not match n = %lld", c->width, c->height, (long long)n);
     return OMERF_ESHAPE;
@@ -338,7 +338,7 @@ static omerf_status validate_camera(const omerf_camera* c, int64_t n) {
   return OMERF_OK;
 }
 
-static Cam to_cam(const omerf_camera* c) {
+Cam to_cam(const omerf_camera* c) {
   Cam k;
   std::memcpy(k.c2w, c->c2w, sizeof(k.c2w));
   k.fx = c->fx;

@@ -1,0 +1,76 @@
+"""The allocation-free render entry point, omerf_render_noalloc, against omerf_render.
+
+It serves callers that cannot allocate device memory: a host framework that
+owns all device memory and hands the renderer fixed buffers, or a frame loop
+that must not call cudaMalloc because it can synchronise the device.  Its
+scratch (work counters, occupancy hulls) lives in one static device array
+shared by every call, so the checks below render several scenes back to back
+and compare each call with the regular entry point.
+
+This file is collected last (test_zz_*) so that a failure here does not hide
+the results of the other GPU tests; it also passes alone in a fresh process.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _util import RGB_ATOL, gpu_scene
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+import paper_2404_09531_gb300 as om  # noqa: E402
+from paper_2404_09531_gb300 import binding  # noqa: E402
+
+
+def _check_same(ref, got, what):
+    rgb_ref, cnt_ref = ref
+    rgb, cnt = got
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(cnt.cpu().numpy(), cnt_ref.cpu().numpy(), err_msg=what)
+    err = (rgb - rgb_ref).abs().max().item() if rgb.numel() else 0.0
+    assert err <= RGB_ATOL, f"{what}: max-abs {err:.3e}"
+
+
+def test_two_calls_in_a_row_match_the_regular_render():
+    sc1 = synth.make_scene(1)
+    s1 = gpu_scene(sc1)
+    cam1 = synth.make_cameras(1)[0]
+    sc2 = synth.make_scene(2)
+    s2 = gpu_scene(sc2)
+    cam2 = synth.make_cameras(2)[0]
+    rays1 = oracle.camera_rays(cam1)[::3]
+    ref1 = om.render(s1, camera=cam1)
+    ref2 = om.render(s2, camera=cam2)
+    ref3 = om.render(s1, rays=rays1)
+    # the caller's own preallocated outputs
+    n1, n2, n3 = 64 * 64, 1920 * 1080, rays1.shape[0]
+    out1 = (torch.empty((n1, 3), device="cuda"), torch.empty(n1, dtype=torch.int32, device="cuda"))
+    out2 = (torch.empty((n2, 3), device="cuda"), torch.empty(n2, dtype=torch.int32, device="cuda"))
+    out3 = (torch.empty((n3, 3), device="cuda"), torch.empty(n3, dtype=torch.int32, device="cuda"))
+    rays1_d = torch.as_tensor(rays1).cuda()
+    for call in range(2):
+        _check_same(ref1, om.render_noalloc(s1, camera=cam1, rgb=out1[0], count=out1[1]), f"scene 1, call {call}")
+        _check_same(ref2, om.render_noalloc(s2, camera=cam2, rgb=out2[0], count=out2[1]), f"scene 2, call {call}")
+        _check_same(ref3, om.render_noalloc(s1, rays=rays1_d, rgb=out3[0], count=out3[1]), f"ray list, call {call}")
+
+
+def test_rejects_an_occupancy_plane_beyond_the_scratch():
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    d = binding._SceneDesc.from_buffer_copy(scene._desc)
+    # a 16384^2 occupancy plane at a fine step needs a 16384^2 coarse grid:
+    # rejected on the host before anything reads the (small) occ array
+    d.occ_res = 16384
+    d.step = 2.0 ** -20
+    rgb = torch.empty((4, 3), device="cuda")
+    rays = torch.as_tensor(oracle.camera_rays(synth.make_cameras(1)[0])[:4]).cuda()
+    lib = om.lib()
+    rc = lib.omerf_render_noalloc(ctypes.byref(d), None, ctypes.c_void_p(rays.data_ptr()), 4,
+                                  ctypes.c_void_p(rgb.data_ptr()), None, None)
+    assert rc == -2
+    assert b"no-allocation render reserves" in lib.omerf_last_error()
