@@ -102,10 +102,13 @@ typedef struct {
 typedef struct omerf_scene omerf_scene;
 
 /* Create a scene handle from a description (validated on the host).  The
- * handle owns small device state only: the occupancy hull used to bound each
- * ray and per-launch work counters.  It builds that state on `stream` and
- * returns without synchronising.  Errors: OMERF_EINVAL / OMERF_ESHAPE for bad
- * descriptions, OMERF_ENOMEM / OMERF_ECUDA if its state cannot be allocated. */
+ * handle owns small device state only: the occupancy hull and coarse
+ * max-pooled occupancy grid used to skip empty space, per-launch work
+ * counters and, for a brick grid, one neighbour record per brick.  It builds
+ * that state on `stream`; for a brick grid it then waits for the stream and
+ * checks that every table entry is -1 or a valid pool index (OMERF_ESHAPE
+ * otherwise).  Errors: OMERF_EINVAL / OMERF_ESHAPE for bad descriptions,
+ * OMERF_ENOMEM / OMERF_ECUDA if its state cannot be allocated. */
 omerf_status omerf_scene_create(const omerf_scene_desc *desc, void *stream, omerf_scene **out);
 
 /* Recompute the scene's occupancy hull after the caller changed occ in
@@ -159,19 +162,22 @@ omerf_status omerf_render(const omerf_scene *scene, const omerf_camera *cam, con
  * device memory -- a host framework that owns all device memory and passes in
  * fixed buffers, or a frame loop that cannot afford cudaMalloc, which may
  * synchronise the device.  It takes the scene description directly (no
- * handle) and keeps its scratch (work counters, occupancy hulls) in a 1 MiB
- * static __device__ array that every GPU loading this library holds until
- * the process exits.  Arguments, layouts and results are those of
- * omerf_render.
+ * handle) and keeps its scratch (work counters, occupancy hulls, brick
+ * neighbour records) in a 1 MiB static __device__ array that every GPU
+ * loading this library holds until the process exits.  Arguments, layouts
+ * and results are those of omerf_render.
  *   - The first call on a device looks up the array's device address with
  *     that device current; make that first call before any stream capture.
- *   - Occupancy planes whose coarse grid does not fit the array are rejected
- *     with OMERF_ESHAPE (the coarse grid has ceil(M / 2^l)^2 cells of 8 bytes,
- *     l the smallest level whose cells span a 32-sample lattice window; about
- *     130,000 cells fit).
+ *   - Scenes whose scratch does not fit are rejected with OMERF_ESHAPE: the
+ *     coarse occupancy grid takes 8 bytes per cell (ceil(M / 2^l)^2 cells, l
+ *     the smallest level whose cells span a 32-sample lattice window) and a
+ *     brick grid 32 bytes per brick; together at most 1,044,224 bytes.
  *   - Every call reuses the same array: calls whose kernels overlap on the GPU
  *     (different streams, or several host threads) race and give wrong
  *     results.  Order them on one stream.
+ *   - Unlike omerf_scene_create it does not check the brick table (that
+ *     needs a synchronising read): every entry must be -1 or a pool index
+ *     below n_bricks.
  *   - It calls no cudaMalloc, cudaFree or other allocating routine. */
 omerf_status omerf_render_noalloc(const omerf_scene_desc *desc, const omerf_camera *cam, const float *rays,
                                   int64_t n, float *rgb, int32_t *count, void *stream);

@@ -43,6 +43,7 @@ struct Geo {
   const float2* occ;
   const float* mlp;
   const float* hull;       // device [2]: min z_min, max z_max over non-empty cells
+  const int* nbr;          // device [n_bricks][8]: pool index of brick b's (+dx, +dy, +dz) neighbours
   const float2* chull;     // device [Mc][Mc]: coarse max-pooled (min z_min, max z_max)
   int clog2;               // coarse cell = 2^clog2 x 2^clog2 occupancy cells
   int Mc;                  // coarse cells per axis
@@ -250,22 +251,31 @@ __device__ __forceinline__ void grid_stencil(const Geo& g, const float p[3], int
 #pragma unroll
     for (int c = 0; c < 8; c++) off[c] = base + ((c >> 2) & 1) * sx + ((c >> 1) & 1) * sy + (c & 1) * sz;
   } else {
+    // brick grid: the base brick's pool index, then its neighbour record
+    // (one 256-bit read) gives the brick of every corner without branching
     const int s = g.blog2, m = (1 << s) - 1, B = 1 << s;
-    int bi = i[0] >> s, bj = i[1] >> s, bk = i[2] >> s;
-    if ((i[0] & m) != m && (i[1] & m) != m && (i[2] & m) != m) {
-      const int b = __ldg(g.table + (bi * g.nb[1] + bj) * g.nb[2] + bk);
-      const int base = ((((b * B + (i[0] & m)) * B + (i[1] & m)) * B) + (i[2] & m)) * kNch;
-      const int sz = kNch, sy = B * kNch, sx = B * B * kNch;
-#pragma unroll
-      for (int c = 0; c < 8; c++)
-        off[c] = b < 0 ? -1 : base + ((c >> 2) & 1) * sx + ((c >> 1) & 1) * sy + (c & 1) * sz;
+    const int b0 = __ldg(g.table + ((i[0] >> s) * g.nb[1] + (i[1] >> s)) * g.nb[2] + (i[2] >> s));
+    int nb[8];
+    if (b0 >= 0) {
+      asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(nb[0]), "=r"(nb[1]), "=r"(nb[2]), "=r"(nb[3]), "=r"(nb[4]), "=r"(nb[5]), "=r"(nb[6]),
+                     "=r"(nb[7])
+                   : "l"(g.nbr + 8 * b0));
     } else {
 #pragma unroll
-      for (int c = 0; c < 8; c++) {
-        int vi = i[0] + ((c >> 2) & 1), vj = i[1] + ((c >> 1) & 1), vk = i[2] + (c & 1);
-        const int b = __ldg(g.table + ((vi >> s) * g.nb[1] + (vj >> s)) * g.nb[2] + (vk >> s));
-        off[c] = b < 0 ? -1 : ((((b * B + (vi & m)) * B + (vj & m)) * B) + (vk & m)) * kNch;
-      }
+      for (int c = 0; c < 8; c++) nb[c] = -1;
+    }
+    const int cx = (i[0] & m) == m, cy = (i[1] & m) == m, cz = (i[2] & m) == m;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      const int dx = (c >> 2) & 1, dy = (c >> 1) & 1, dz = c & 1;
+      // neighbour slot: the axes on which this corner leaves the base brick
+      const int kx = dx & cx, ky = dy & cy, kz = dz & cz;
+      const int z0 = kz ? nb[1] : nb[0], z1 = kz ? nb[3] : nb[2], z2 = kz ? nb[5] : nb[4], z3 = kz ? nb[7] : nb[6];
+      const int y0 = ky ? z1 : z0, y1 = ky ? z3 : z2;
+      const int b = kx ? y1 : y0;
+      const int li = (i[0] + dx) & m, lj = (i[1] + dy) & m, lk = (i[2] + dz) & m;
+      off[c] = b < 0 ? -1 : ((((b * B + li) * B + lj) * B) + lk) * kNch;
     }
   }
 }

@@ -12,6 +12,7 @@ struct omerf_scene {
   float* state = nullptr;          // device: [0..1] occupancy hull (min z_min, max z_max)
   unsigned* counters = nullptr;    // device: per-launch work counters
   float2* chull = nullptr;         // device: coarse max-pooled occupancy grid [Mc][Mc]
+  int* nbr = nullptr;              // device: brick neighbour records [n_bricks][8] (brick grids)
   int clog2 = 0, Mc = 1;
   mutable std::atomic<unsigned> seq{0};
   int device = 0;
@@ -47,6 +48,7 @@ omerf_status cuda_fail(cudaError_t e, const char* what);
 omerf_status validate_desc(const omerf_scene_desc* d);
 void fill_geo(omerf_scene* s);
 void choose_coarse_level(omerf_scene* s);
+omerf_status build_brick_neighbors(omerf_scene* s, cudaStream_t stream);
 omerf_status validate_camera(const omerf_camera* c, int64_t n);
 omerf::Cam to_cam(const omerf_camera* c);
 

@@ -15,12 +15,12 @@
 
 namespace omerf {
 
-// Scratch layout: work counters | occupancy hull (2 floats) | coarse grid.
+// Scratch layout: work counters | occupancy hull (2 floats) | coarse grid |
+// brick neighbour records (brick grids).
 constexpr size_t kNoAllocCounterBytes = kCounterSlots * sizeof(unsigned);
 constexpr size_t kNoAllocHullOffset = kNoAllocCounterBytes;
 constexpr size_t kNoAllocCoarseOffset = kNoAllocHullOffset + 256;
 constexpr size_t kNoAllocScratchBytes = 1u << 20;  // 1 MiB
-constexpr size_t kNoAllocCoarseMaxCells = (kNoAllocScratchBytes - kNoAllocCoarseOffset) / sizeof(float2);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -80,11 +80,14 @@ extern "C" omerf_status omerf_render_noalloc(const omerf_scene_desc* desc, const
   s.desc = *desc;
   choose_coarse_level(&s);
   const size_t cells = (size_t)s.Mc * (size_t)s.Mc;
-  if (cells > kNoAllocCoarseMaxCells) {
-    set_error("occupancy plane of %d x %d cells needs a %d x %d coarse grid (%zu bytes), more than the %zu bytes the "
-              "no-allocation render reserves for it",
-              desc->occ_res, desc->occ_res, s.Mc, s.Mc, cells * sizeof(float2),
-              kNoAllocCoarseMaxCells * sizeof(float2));
+  const size_t coarse_bytes = (cells * sizeof(float2) + 255) / 256 * 256;
+  const size_t nbr_offset = kNoAllocCoarseOffset + coarse_bytes;
+  const size_t nbr_bytes = desc->brick ? (size_t)desc->n_bricks * 8 * sizeof(int) : 0;
+  if (nbr_offset + nbr_bytes > kNoAllocScratchBytes) {
+    set_error("a %d x %d occupancy plane (%zu-byte coarse grid) with %d bricks (%zu bytes of neighbour records) needs "
+              "more than the %zu bytes the no-allocation render reserves",
+              desc->occ_res, desc->occ_res, coarse_bytes, desc->brick ? desc->n_bricks : 0, nbr_bytes,
+              kNoAllocScratchBytes - kNoAllocCoarseOffset);
     return OMERF_ESHAPE;
   }
   cudaError_t e = cudaGetDevice(&s.device);
@@ -100,10 +103,12 @@ extern "C" omerf_status omerf_render_noalloc(const omerf_scene_desc* desc, const
   s.counters = reinterpret_cast<unsigned*>(scratch);
   s.state = reinterpret_cast<float*>(scratch + kNoAllocHullOffset);
   s.chull = reinterpret_cast<float2*>(scratch + kNoAllocCoarseOffset);
+  s.nbr = nbr_bytes ? reinterpret_cast<int*>(scratch + nbr_offset) : nullptr;
   fill_geo(&s);
   if (n == 0) return OMERF_OK;
-  // Every call rebuilds the hulls: the array keeps whatever the previous
-  // call (of any scene) left in it.  The work counter is zeroed by the launch.
+  // Every call rebuilds the hulls and neighbour records: the array keeps
+  // whatever the previous call (of any scene) left in it.  The work counter
+  // is zeroed by the launch.
   cudaStream_t cs = (cudaStream_t)stream;
   const long occ_cells = (long)desc->occ_res * desc->occ_res;
   hull_kernel<<<1, 1024, 0, cs>>>(s.geo.occ, occ_cells, s.state);
@@ -111,6 +116,7 @@ extern "C" omerf_status omerf_render_noalloc(const omerf_scene_desc* desc, const
                                                                       s.chull);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "no-allocation hull kernels");
+  if (nbr_bytes && (st = build_brick_neighbors(&s, cs)) != OMERF_OK) return st;
   e = launch_march_fwd(&s, cam ? &k : nullptr, rays, n, rgb, count, nullptr, nullptr, 0, nullptr, nullptr, nullptr,
                        cs);
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "no-allocation render launch");

@@ -120,6 +120,33 @@ __global__ void brick_flag_kernel(const BrickArgs a, long total) {
   a.table[id] = hit;
 }
 
+// Neighbour records of a brick grid: for each allocated brick b at brick
+// coordinates (bi, bj, bk), nbr[b][dx*4 + dy*2 + dz] is the pool index of the
+// brick at (bi + dx, bj + dy, bk + dz), -1 if unallocated or outside.
+__global__ void brick_neighbor_kernel(const int* __restrict__ table, int nbx, int nby, int nbz, int n_bricks,
+                                      int* __restrict__ nbr) {
+  const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long)nbx * nby * nbz) return;
+  const int b = table[id];
+  if (b < 0 || b >= n_bricks) return;
+  const int bk = (int)(id % nbz), bj = (int)((id / nbz) % nby), bi = (int)(id / ((long)nbz * nby));
+  for (int c = 0; c < 8; c++) {
+    const int x = bi + ((c >> 2) & 1), y = bj + ((c >> 1) & 1), z = bk + (c & 1);
+    int v = -1;
+    if (x < nbx && y < nby && z < nbz) v = table[((long)x * nby + y) * nbz + z];
+    nbr[8l * b + c] = v;
+  }
+}
+
+// Count brick-table entries that are neither -1 nor a pool index.
+__global__ void brick_table_check_kernel(const int* __restrict__ table, long total, int n_bricks,
+                                         unsigned* __restrict__ bad) {
+  const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= total) return;
+  const int b = table[id];
+  if (b < -1 || b >= n_bricks) atomicAdd(bad, 1u);
+}
+
 // In-place exclusive scan of the 0/1 flags into pool indices (-1 = empty),
 // one CTA, each thread owning a contiguous segment (x-major brick order).
 __global__ void brick_scan_kernel(int* table, long total, int* n_alloc) {
@@ -312,8 +339,21 @@ void fill_geo(omerf_scene* s) {
   g.mlp = d.mlp;
   g.hull = s->state;
   g.chull = s->chull;
+  g.nbr = s->nbr;
   g.clog2 = s->clog2;
   g.Mc = s->Mc;
+}
+
+omerf_status build_brick_neighbors(omerf_scene* s, cudaStream_t stream) {
+  const Geo& g = s->geo;
+  const long total = (long)g.nb[0] * g.nb[1] * g.nb[2];
+  cudaError_t e = cudaMemsetAsync(s->nbr, 0xff, (size_t)s->desc.n_bricks * 8 * sizeof(int), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "neighbour table memset");
+  if (total > 0)
+    brick_neighbor_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(s->desc.brick_table, g.nb[0], g.nb[1],
+                                                                              g.nb[2], s->desc.n_bricks, s->nbr);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "neighbour table kernel");
 }
 
 // Coarse level: the smallest power-of-two block of occupancy cells whose side
@@ -379,15 +419,43 @@ omerf_status omerf_scene_create(const omerf_scene_desc* desc, void* stream, omer
   if (e != cudaSuccess) { cudaGetLastError(); cudaFree(s->state); delete s; set_error("cudaMalloc: %s", cudaGetErrorString(e)); return OMERF_ENOMEM; }
   choose_coarse_level(s);
   e = cudaMalloc(&s->chull, (size_t)s->Mc * s->Mc * sizeof(float2));
+  if (e == cudaSuccess && desc->brick && desc->n_bricks > 0)
+    e = cudaMalloc(&s->nbr, (size_t)desc->n_bricks * 8 * sizeof(int));
   if (e != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(s->state);
-    cudaFree(s->counters);
-    delete s;
+    omerf_scene_destroy(s);
     set_error("cudaMalloc: %s", cudaGetErrorString(e));
     return OMERF_ENOMEM;
   }
   fill_geo(s);
+  if (desc->brick) {
+    // a table entry outside the pool would make the march read outside it
+    const long total = (long)s->geo.nb[0] * s->geo.nb[1] * s->geo.nb[2];
+    unsigned* bad = s->counters;  // counter slot 0 doubles as the check result
+    cudaStream_t cs = (cudaStream_t)stream;
+    unsigned nbad = 0;
+    e = cudaMemsetAsync(bad, 0, sizeof(unsigned), cs);
+    if (e == cudaSuccess && total > 0) {
+      brick_table_check_kernel<<<(unsigned)((total + 255) / 256), 256, 0, cs>>>(desc->brick_table, total,
+                                                                                desc->n_bricks, bad);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+      omerf_scene_destroy(s);
+      return cuda_fail(e, "brick table check");
+    }
+    if (nbad) {
+      omerf_scene_destroy(s);
+      set_error("the brick table holds %u entries outside [-1, n_bricks = %d)", nbad, desc->n_bricks);
+      return OMERF_ESHAPE;
+    }
+    if (desc->n_bricks > 0 && (st = build_brick_neighbors(s, cs)) != OMERF_OK) {
+      omerf_scene_destroy(s);
+      return st;
+    }
+  }
   st = omerf_scene_update(s, stream);
   if (st != OMERF_OK) { omerf_scene_destroy(s); return st; }
   *out = s;
@@ -410,6 +478,7 @@ void omerf_scene_destroy(omerf_scene* s) {
   cudaFree(s->state);
   cudaFree(s->counters);
   cudaFree(s->chull);
+  cudaFree(s->nbr);
   delete s;
 }
 
