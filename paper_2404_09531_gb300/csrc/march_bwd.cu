@@ -185,11 +185,14 @@ struct WarpBwd {
 template <class FT, bool SPARSE>
 __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a, int lane, const float o[3],
                                                  const float d[3], int klo, int khi, bool live, WarpBwd& ws) {
-  const int mycnt = ws.cnt[lane];
+  ws.q.ro[lane] = make_float4(o[0], o[1], o[2], __int_as_float(klo));
+  ws.q.rd[lane] = make_float4(d[0], d[1], d[2], __int_as_float(khi));
+  ws.q.cap[lane] = ws.cnt[lane];
   unsigned pend = __ballot_sync(kFull, live);
   FillState f;
+  __syncwarp();
   while (pend) {
-    const int nq = fill_queue(g, lane, o, d, klo, khi, mycnt, pend, f, ws.q);
+    const int nq = fill_queue(g, lane, pend, f, ws.q);
     if (nq == 0) break;
     const bool act = lane < nq;
     const float4 qa = ws.q.a[lane], qb = ws.q.b[lane];

@@ -41,11 +41,14 @@ __device__ __forceinline__ void march_bundle(const Geo& g, int lane, const float
   for (int c = 0; c < 8; c++) ws.F[lane][c] = 0.0f;
   ws.T[lane] = 1.0f;
   ws.cnt[lane] = 0;
+  ws.q.ro[lane] = make_float4(o[0], o[1], o[2], __int_as_float(klo));
+  ws.q.rd[lane] = make_float4(d[0], d[1], d[2], __int_as_float(khi));
+  ws.q.cap[lane] = g.n_max;
   unsigned pend = __ballot_sync(kFull, any);
   FillState f;
   __syncwarp();
   while (pend) {
-    const int nq = fill_queue(g, lane, o, d, klo, khi, g.n_max, pend, f, ws.q);
+    const int nq = fill_queue(g, lane, pend, f, ws.q);
     if (nq == 0) break;
     const bool act = lane < nq;
     const float4 qa = ws.q.a[lane], qb = ws.q.b[lane];
@@ -98,9 +101,9 @@ __device__ __forceinline__ void march_bundle(const Geo& g, int lane, const float
 
 struct FwdArgs {
   Cam cam;
-  int use_cam, tiles_x;
+  int use_cam, super_x;
   const float* rays;
-  long n, n_bundles;
+  long n, n_super;
   float* rgb;
   int* count;
   // training
@@ -128,23 +131,30 @@ __global__ void __launch_bounds__(kThreads, OMERF_FWD_MINB) march_fwd_kernel(con
   WarpMarch& ws = sMarch[threadIdx.x >> 5];
   float l_rgb = 0.0f, l_smooth = 0.0f;
 
+  // The CTA takes work in units of 8 bundles so that its 8 warps march
+  // neighbouring rays together and share L1 lines: a camera super-tile of
+  // 2 x 4 tiles of 8 x 4 pixels (16 x 16 pixels), or 256 consecutive rays.
+  __shared__ unsigned sWork;
+  const int warp = threadIdx.x >> 5;
   for (;;) {
-    unsigned b = 0;
-    if (lane == 0) b = atomicAdd(a.counter, 1u);
-    b = __shfl_sync(kFull, b, 0);
-    if (b >= a.n_bundles) break;
+    if (threadIdx.x == 0) sWork = atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const unsigned sb = sWork;
+    __syncthreads();
+    if (sb >= a.n_super) break;
 
     long rid;
     bool valid;
     float o[3] = {0.0f, 0.0f, 0.0f}, d[3] = {0.0f, 0.0f, 1.0f};
     if (a.use_cam) {
-      const int tx = (int)(b % (unsigned)a.tiles_x), ty = (int)(b / (unsigned)a.tiles_x);
+      const int sx = (int)(sb % (unsigned)a.super_x), sy = (int)(sb / (unsigned)a.super_x);
+      const int tx = 2 * sx + (warp & 1), ty = 4 * sy + (warp >> 1);
       const int px = tx * 8 + (lane & 7), py = ty * 4 + (lane >> 3);
       valid = px < a.cam.width && py < a.cam.height;
       rid = (long)py * a.cam.width + px;
       if (valid) camera_ray(a.cam, px, py, o, d);
     } else {
-      rid = (long)b * 32 + lane;
+      rid = ((long)sb * 8 + warp) * 32 + lane;
       valid = rid < a.n;
       if (valid) {
         const float* r = a.rays + 6 * rid;
@@ -247,7 +257,7 @@ static cudaError_t launch_variant(const omerf_scene* s, const FwdArgs& a, cudaSt
   static int blocks[64] = {0};
   const int dev = s->device & 63;
   if (blocks[dev] == 0) blocks[dev] = persistent_blocks((const void*)kern, kThreads, 0, s->num_sms);
-  long want = (a.n_bundles + (kThreads / 32) - 1) / (kThreads / 32);
+  long want = a.n_super;
   int grid = (int)(want < blocks[dev] ? want : blocks[dev]);
   if (grid < 1) grid = 1;
   kern<<<grid, kThreads, 0, stream>>>(s->geo, a);
@@ -262,11 +272,11 @@ cudaError_t launch_march_fwd(const omerf_scene* s, const Cam* cam, const float* 
   if (cam) {
     a.cam = *cam;
     a.use_cam = 1;
-    a.tiles_x = (cam->width + 7) / 8;
-    a.n_bundles = (long)a.tiles_x * ((cam->height + 3) / 4);
+    a.super_x = (cam->width + 15) / 16;
+    a.n_super = (long)a.super_x * ((cam->height + 15) / 16);
   } else {
     a.use_cam = 0;
-    a.n_bundles = (n + 31) / 32;
+    a.n_super = (n + 255) / 256;
   }
   a.rays = rays;
   a.n = n;
@@ -281,7 +291,7 @@ cudaError_t launch_march_fwd(const omerf_scene* s, const Cam* cam, const float* 
   }
   a.saved = saved;
   a.loss = loss;
-  if (a.n_bundles == 0) return cudaSuccess;
+  if (a.n_super == 0) return cudaSuccess;
   a.counter = next_counter(s, stream);
   const bool bf16 = s->desc.feat_dtype == OMERF_BF16;
   const bool sparse = s->desc.brick > 0;

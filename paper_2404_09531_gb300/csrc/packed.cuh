@@ -14,10 +14,14 @@
 
 namespace omerf {
 
-// One queued sample: position, occupancy interval, ray slot, occupancy cell.
+// One queued sample: position, occupancy interval, ray slot, occupancy cell;
+// plus the bundle's rays (kept in shared memory, not registers).
 struct WarpQueue {
-  float4 a[32];  // p.x, p.y, p.z, z_min
-  float4 b[32];  // z_max, ray slot (int bits), cell (int bits), unused
+  float4 a[32];   // p.x, p.y, p.z, z_min
+  float4 b[32];   // z_max, ray slot (int bits), cell (int bits), unused
+  float4 ro[32];  // ray origin, first lattice index (int bits)
+  float4 rd[32];  // ray direction, last lattice index (int bits)
+  int cap[32];    // maximum samples of the ray
 };
 
 // Warp-uniform state of the ray currently being filled.
@@ -31,23 +35,25 @@ struct FillState {
 
 // Append evaluated samples to the queue until it holds 32 or no pending ray
 // is left.  pend: bitmask of rays with candidates left (the lowest is filled
-// first; callers clear bits of rays that stop early).  cap: per-lane maximum
-// number of samples of the lane's ray.  Returns the number of queued samples.
-__device__ __forceinline__ int fill_queue(const Geo& g, int lane, const float o[3], const float d[3], int klo,
-                                          int khi, int cap, unsigned& pend, FillState& f, WarpQueue& q) {
+// first; callers clear bits of rays that stop early).  The rays (origin,
+// direction, lattice range, sample cap) are read from q.ro / q.rd / q.cap.
+// Returns the number of queued samples.
+__device__ __forceinline__ int fill_queue(const Geo& g, int lane, unsigned& pend, FillState& f, WarpQueue& q) {
   int nq = 0;
   while (nq < 32 && pend) {
     const int nxt = __ffs(pend) - 1;
     if (f.cur != nxt) {
       f.cur = nxt;
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        f.o[c] = __shfl_sync(kFull, o[c], nxt);
-        f.d[c] = __shfl_sync(kFull, d[c], nxt);
-      }
-      f.kn = __shfl_sync(kFull, klo, nxt);
-      f.kh = __shfl_sync(kFull, khi, nxt);
-      f.cap = __shfl_sync(kFull, cap, nxt);
+      const float4 ro = q.ro[nxt], rd = q.rd[nxt];
+      f.o[0] = ro.x;
+      f.o[1] = ro.y;
+      f.o[2] = ro.z;
+      f.d[0] = rd.x;
+      f.d[1] = rd.y;
+      f.d[2] = rd.z;
+      f.kn = __float_as_int(ro.w);
+      f.kh = __float_as_int(rd.w);
+      f.cap = q.cap[nxt];
       f.qc = 0;
       f.wbase = f.kn;
       f.wmask = window_mask(g, f.o, f.d, f.wbase, f.kh, lane);
