@@ -34,10 +34,11 @@ import synth  # noqa: E402
 
 BYTES_PER_SAMPLE = {"f32": 640 + 8, "bf16": 320 + 8}  # feature gather + occupancy bounds
 BYTES_PER_RAY_RENDER = 12 + 4                          # rgb + count written
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel,
-# from the ncu capture summarised in profiles/ (None until captured for the
-# current kernel version).
-TRAFFIC_PER_LAUNCH = None
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel
+# (one 1920x1080 frame of march_fwd_kernel<float, sparse, render>), from the ncu
+# capture summarised in profiles/march_fwd_render1080_sparse_f32.md; set to None
+# whenever that kernel changes until it is captured again.
+TRAFFIC_PER_LAUNCH = 53.404416e6 + 6.373376e6
 
 
 def _peaks():
