@@ -183,6 +183,88 @@ def cpu_baseline_sample(sc, cams, budget_s=12.0):
 
 
 # ---------------------------------------------------------------------------
+# secondary workloads reported in the same line: BF16 vs FP32
+# ---------------------------------------------------------------------------
+def _time_renders(om, torch, scene, cams, steps, warmup, flush, stream):
+    for _ in range(warmup):
+        for cam in cams:
+            om.render(scene, camera=cam, want_count=False)
+    ms = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in cams]
+        for (a, b), cam in zip(ev, cams):
+            a.record(stream)
+            om.render(scene, camera=cam, want_count=False)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(sum(a.elapsed_time(b) for a, b in ev))
+    return float(np.mean(ms))
+
+
+def bench_precision_render(om, torch, dev, steps, warmup, flush, stream):
+    """3840x2160 x 4 cameras, BF16 features + tensor-core MLP vs FP32 features,
+    same scene; PSNR of the BF16 frames against the FP32 frames."""
+    sc = synth.make_scene(4)
+    spec = sc["spec"]
+    occ = torch.as_tensor(sc["occ"]).to(dev)
+    table = om.build_brick_table(spec.aabb, spec.L, spec.brick, occ)[0].cpu().numpy()
+    cams = synth.make_cameras(4)
+    rays = sum(c["width"] * c["height"] for c in cams)
+    out = {"workload": "render 4 oblique cameras 3840x2160, sparse 1024x1024x64 grid (8^3 bricks, 9.6% "
+                       "allocated), planes 4096^2 / 4096x256, occupancy 512^2, step 1/2048",
+           "rays_per_step": rays}
+    frames = {}
+    for name, dt in (("bf16", torch.bfloat16), ("f32", torch.float32)):
+        scene = om.scene_from_synth(sc, device=dev, table=table, feat_dtype=dt)
+        t = _time_renders(om, torch, scene, cams, steps, warmup, flush, stream)
+        frames[name] = om.render(scene, camera=cams[0])[0]
+        out[name] = {"value": rays / (t * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": t}
+        del scene
+    mse = float(((frames["bf16"] - frames["f32"]) ** 2).mean().item())
+    out["psnr_bf16_vs_f32_db"] = 10.0 * np.log10(1.0 / mse) if mse > 0 else float("inf")
+    out["speedup_bf16_over_f32"] = out["bf16"]["value"] / out["f32"]["value"]
+    return out
+
+
+def bench_precision_train(om, torch, dev, steps, warmup, flush, stream, n_rays=1 << 20):
+    """Training fwd+bwd on 2^20 rays of 64 cameras, BF16 features (FP32 gradients)
+    vs FP32 features, 64x64x16 grid / 256^2, 256x32 planes."""
+    sc = synth.make_scene(5)
+    batch = synth.make_train_batch(5, n_rays)
+    rays_d = torch.as_tensor(batch["rays"]).to(dev)
+    dirs_d = torch.as_tensor(batch["smooth_dirs"]).to(dev)
+    tgt_d = torch.as_tensor(batch["target"]).to(dev)
+    lam = (1.0, 1e-2, 1e-4)
+    out = {"workload": "fwd+bwd 2^20 rays of 64 cameras, 64x64x16 grid, 256^2/256x32 planes, K=1",
+           "rays_per_step": n_rays}
+    for name, dt in (("bf16", torch.bfloat16), ("f32", torch.float32)):
+        scene = om.scene_from_synth(sc, device=dev, feat_dtype=dt)
+        grads = om.binding._zero_grads(scene)
+        saved = torch.empty(n_rays * om.saved_bytes_per_ray() // 4, dtype=torch.float32, device=dev)
+        for _ in range(warmup):
+            om.train_step(scene, rays_d, tgt_d, dirs_d, lam=lam, grads=grads, saved=saved)
+        torch.cuda.reset_peak_memory_stats(dev)
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            for gt in grads.values():
+                gt.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            om.train_step(scene, rays_d, tgt_d, dirs_d, lam=lam, grads=grads, saved=saved)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = float(np.mean(ms))
+        feat_bytes = sum(x.numel() * x.element_size() for x in (scene.grid, scene.p_xy, scene.p_xz, scene.p_yz))
+        out[name] = {"value": n_rays / (t * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": t,
+                     "feature_bytes": feat_bytes}
+        del scene, grads, saved
+    return out
+
+
+# ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
 def run_native(args):
@@ -299,6 +381,12 @@ def run_native(args):
     t_train = float(np.mean(tr_ms))
     loss = res["loss"].cpu().numpy().tolist()
 
+    precision = None
+    if not args.no_precision:
+        psteps = max(1, min(args.steps, 5))
+        precision = {"render": bench_precision_render(om, torch, dev, psteps, args.warmup, flush, stream),
+                     "train": bench_precision_train(om, torch, dev, psteps, args.warmup, flush, stream)}
+
     if rank != 0:
         return 0
 
@@ -328,6 +416,8 @@ def run_native(args):
         "gpu_launches": args.steps * len(cams),
         "clocks": clk,
     }
+    if precision is not None:
+        line["precision"] = precision
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(sc, cams)
     print(json.dumps(line), flush=True)
@@ -344,6 +434,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the BF16 vs FP32 workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -11,14 +11,26 @@
 // deferred MLP (Eq. 4).
 #include <cstdio>
 
+#include <type_traits>
+
 #include "internal.h"
+#include "mlp_mma.cuh"
 #include "packed.cuh"
 
 namespace omerf {
 
-// Per-warp shared state of the packed march of one bundle of 32 rays.
-struct WarpMarch {
+// Per-warp shared state of the packed march of one bundle of 32 rays.  With
+// the tensor-core MLP the sample queue doubles as the MLP staging area.
+struct QueueOnly {
   WarpQueue q;
+};
+union QueueOrStage {
+  WarpQueue q;
+  MlpStage m;
+};
+template <bool MMA>
+struct WarpMarch {
+  typename std::conditional<MMA, QueueOrStage, QueueOnly>::type u;
   float F[32][8];    // per-ray accumulated [sum w c^d, sum w f]
   float T[32];       // per-ray transmittance so far
   int cnt[32];       // per-ray evaluated samples
@@ -34,24 +46,24 @@ struct WarpMarch {
 //          the weighted features are summed per segment into the ray's
 //          accumulator.
 // On return ws.F / ws.T / ws.cnt hold every ray's F, T_N and sample count.
-template <class FT, bool SPARSE>
+template <class FT, bool SPARSE, class WS>
 __device__ __forceinline__ void march_bundle(const Geo& g, int lane, const float o[3], const float d[3], int klo,
-                                             int khi, bool any, WarpMarch& ws) {
+                                             int khi, bool any, WS& ws) {
 #pragma unroll
   for (int c = 0; c < 8; c++) ws.F[lane][c] = 0.0f;
   ws.T[lane] = 1.0f;
   ws.cnt[lane] = 0;
-  ws.q.ro[lane] = make_float4(o[0], o[1], o[2], __int_as_float(klo));
-  ws.q.rd[lane] = make_float4(d[0], d[1], d[2], __int_as_float(khi));
-  ws.q.cap[lane] = g.n_max;
+  ws.u.q.ro[lane] = make_float4(o[0], o[1], o[2], __int_as_float(klo));
+  ws.u.q.rd[lane] = make_float4(d[0], d[1], d[2], __int_as_float(khi));
+  ws.u.q.cap[lane] = g.n_max;
   unsigned pend = __ballot_sync(kFull, any);
   FillState f;
   __syncwarp();
   while (pend) {
-    const int nq = fill_queue(g, lane, pend, f, ws.q);
+    const int nq = fill_queue(g, lane, pend, f, ws.u.q);
     if (nq == 0) break;
     const bool act = lane < nq;
-    const float4 qa = ws.q.a[lane], qb = ws.q.b[lane];
+    const float4 qa = ws.u.q.a[lane], qb = ws.u.q.b[lane];
     const int r = act ? __float_as_int(qb.y) : 32;
     SampleAct s;
     s.ah = 0.0f;
@@ -122,13 +134,20 @@ struct FwdArgs {
 
 template <class FT, bool SPARSE, bool TRAIN>
 __global__ void __launch_bounds__(kThreads, OMERF_FWD_MINB) march_fwd_kernel(const Geo g, const FwdArgs a) {
-  __shared__ __align__(16) float sW[kSmemMlp];
+  // BF16 render: deferred MLP on tensor cores; otherwise FP32 on CUDA cores
+  constexpr bool kMMA = std::is_same<FT, __nv_bfloat16>::value && !TRAIN;
+  __shared__ __align__(16) float sW[kMMA ? 4 : kSmemMlp];
+  __shared__ typename std::conditional<kMMA, MlpFrags, int>::type sFrag;
   __shared__ float sLoss[2][kThreads / 32];
-  __shared__ WarpMarch sMarch[kThreads / 32];
-  load_mlp_padded(g.mlp, sW);
+  __shared__ WarpMarch<kMMA> sMarch[kThreads / 32];
+  if constexpr (kMMA) {
+    build_mlp_frags(g.mlp, sFrag);
+  } else {
+    load_mlp_padded(g.mlp, sW);
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  WarpMarch& ws = sMarch[threadIdx.x >> 5];
+  WarpMarch<kMMA>& ws = sMarch[threadIdx.x >> 5];
   float l_rgb = 0.0f, l_smooth = 0.0f;
 
   // The CTA takes work in units of 8 bundles so that its 8 warps march
@@ -175,13 +194,23 @@ __global__ void __launch_bounds__(kThreads, OMERF_FWD_MINB) march_fwd_kernel(con
     const int cnt = ws.cnt[lane];
     __syncwarp();
 
+    float yd_mma[3] = {0.0f, 0.0f, 0.0f};
+    if constexpr (kMMA) {
+      mlp_stage_row(ws.u.m, lane, valid && cnt > 0, F, d);
+      mlp_bf16_warp(sFrag, ws.u.m, lane, yd_mma);
+    }
     if (valid) {
       float out[3], yd[3] = {0.0f, 0.0f, 0.0f};
       if (cnt == 0) {
 #pragma unroll
         for (int j = 0; j < 3; j++) out[j] = g.bg[j];
       } else {
-        mlp_forward_padded(sW, F, d, yd);
+        if constexpr (kMMA) {
+#pragma unroll
+          for (int j = 0; j < 3; j++) yd[j] = yd_mma[j];
+        } else {
+          mlp_forward_padded(sW, F, d, yd);
+        }
 #pragma unroll
         for (int j = 0; j < 3; j++) out[j] = F[j] + yd[j] + T * g.bg[j];
       }

@@ -191,8 +191,10 @@ def test_config2_full_frames_sampled_pixels():
 
 
 def test_config4_bf16_psnr():
-    """BF16 features vs the FP64 oracle on the original FP32 features (PSNR >= 45 dB)
-    and on the BF16-rounded features (arithmetic error only)."""
+    """BF16 features and the BF16 tensor-core deferred MLP vs the FP64 oracle on
+    the original FP32 features (PSNR >= 45 dB), and vs the oracle on the
+    BF16-rounded features, where only the arithmetic differs: counts equal,
+    and the MLP's BF16 operands (8-bit mantissa) bound the colour error."""
     sc = synth.make_scene(4)
     table, pool = brick_inputs(sc)
     scene = gpu_scene(sc, table=table)
@@ -209,4 +211,19 @@ def test_config4_bf16_psnr():
     ref_b = oracle.render(oracle_scene_for(sc_b, table=table, pool=rb(pool)), rays[idx])
     ok = (ref_b["ambiguous"] == 0) & (ref["ambiguous"] == 0)
     assert np.array_equal(cnt[idx][ok], ref_b["count"][ok])
-    assert np.abs(rgb[idx][ok] - ref_b["rgb"][ok]).max() <= 5e-4
+    assert psnr(rgb[idx][ok], ref_b["rgb"][ok]) >= 55.0
+    assert np.abs(rgb[idx][ok] - ref_b["rgb"][ok]).max() <= 1e-2
+
+
+def test_config4_fp32_full_size_sampled_pixels():
+    """The same 3840x2160 scene with FP32 features: counts bit-exact and rgb
+    max-abs <= 1e-4 on every 127th pixel of a frame."""
+    sc = synth.make_scene(4)
+    table, pool = brick_inputs(sc)
+    scene = gpu_scene(sc, table=table, feat_dtype=torch.float32)
+    cam = synth.make_cameras(4)[1]
+    rgb, cnt = _render_np(scene, camera=cam)
+    rays = oracle.camera_rays(cam)
+    idx = np.arange(0, rays.shape[0], 127)
+    ref = oracle.render(oracle_scene_for(sc, table=table, pool=pool), rays[idx])
+    compare_render(rgb[idx], cnt[idx], ref, what="config 4 fp32")
