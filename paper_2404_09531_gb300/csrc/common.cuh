@@ -165,7 +165,14 @@ __device__ __forceinline__ unsigned window_mask(const Geo& g, const float o[3], 
       const int cy0 = min(max((int)floorf(__fmul_rn(__fsub_rn(fmaxf(lo[1], g.lo[1]), g.lo[1]), g.osy)), 0), g.M - 1);
       const int cy1 = min(max((int)floorf(__fmul_rn(__fsub_rn(fminf(hi[1], g.hi[1]), g.lo[1]), g.osy)), 0), g.M - 1);
       const int X0 = cx0 >> g.clog2, X1 = cx1 >> g.clog2, Y0 = cy0 >> g.clog2, Y1 = cy1 >> g.clog2;
-      if ((X1 - X0 + 1) * (Y1 - Y0 + 1) > 16) {
+      if (X1 - X0 <= 1 && Y1 - Y0 <= 1) {
+        // the common case: at most 2 x 2 coarse cells, read independently
+        const float2 h00 = __ldg(g.chull + X0 * g.Mc + Y0), h01 = __ldg(g.chull + X0 * g.Mc + Y1);
+        const float2 h10 = __ldg(g.chull + X1 * g.Mc + Y0), h11 = __ldg(g.chull + X1 * g.Mc + Y1);
+        const float zl = fminf(fminf(h00.x, h01.x), fminf(h10.x, h11.x));
+        const float zh = fmaxf(fmaxf(h00.y, h01.y), fmaxf(h10.y, h11.y));
+        maybe = zl <= hi[2] && zh >= lo[2];
+      } else if ((X1 - X0 + 1) * (Y1 - Y0 + 1) > 16) {
         maybe = true;  // unusually long window in cell units: keep it
       } else {
         for (int X = X0; X <= X1 && !maybe; X++)
