@@ -109,6 +109,26 @@ def _dist():
     return ws, rank, local
 
 
+def rank_cameras(rank: int):
+    """Ray sharding across ranks: rank r renders its own 8 seeded oblique
+    cameras of the same scene (rank 0 renders the default set), so per-rank
+    work is fixed as ranks are added (weak scaling) and no rank needs another
+    rank's data."""
+    return synth.make_cameras(2) if rank == 0 else synth.make_cameras(2, seed=2 + 7919 * rank)
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The slowest rank's step time (the job's time); identity on one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _workload_config():
     spec = synth.scene_spec(2)
     return {"workload": "render 8 oblique cameras 1920x1080, sparse 512x512x32 grid (8^3 bricks, "
@@ -116,6 +136,7 @@ def _workload_config():
                         "n_max 512, FP32 features",
             "rays_per_step": spec.n_cams * spec.width * spec.height,
             "l2": "flushed between steps (256 MiB write)",
+            "parallelism": "ray sharding: each rank renders its own 8 cameras, no data exchange",
             "train_workload": "fwd+bwd 2^18 rays, 64x64x16 grid, 256^2/256x32 planes, occupancy 32^2, "
                               "step 1/256, K=1 smoothness direction, FP32"}
 
@@ -237,14 +258,18 @@ def bench_precision_train(om, torch, dev, steps, warmup, flush, stream, n_rays=1
     tgt_d = torch.as_tensor(batch["target"]).to(dev)
     lam = (1.0, 1e-2, 1e-4)
     out = {"workload": "fwd+bwd 2^20 rays of 64 cameras, 64x64x16 grid, 256^2/256x32 planes, K=1",
-           "rays_per_step": n_rays}
+           "rays_per_step": n_rays,
+           "peak_device_bytes_note": "torch allocations of the form (features, FP32 gradients, rays, targets, "
+                                     "smoothness directions, saved state); the batch (~92 MB) is shared"}
     for name, dt in (("bf16", torch.bfloat16), ("f32", torch.float32)):
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats(dev)
         scene = om.scene_from_synth(sc, device=dev, feat_dtype=dt)
         grads = om.binding._zero_grads(scene)
         saved = torch.empty(n_rays * om.saved_bytes_per_ray() // 4, dtype=torch.float32, device=dev)
         for _ in range(warmup):
             om.train_step(scene, rays_d, tgt_d, dirs_d, lam=lam, grads=grads, saved=saved)
-        torch.cuda.reset_peak_memory_stats(dev)
         ms = []
         for _ in range(steps):
             flush.fill_(1.0)
@@ -259,7 +284,8 @@ def bench_precision_train(om, torch, dev, steps, warmup, flush, stream, n_rays=1
         t = float(np.mean(ms))
         feat_bytes = sum(x.numel() * x.element_size() for x in (scene.grid, scene.p_xy, scene.p_xz, scene.p_yz))
         out[name] = {"value": n_rays / (t * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": t,
-                     "feature_bytes": feat_bytes}
+                     "feature_bytes": feat_bytes,
+                     "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev))}
         del scene, grads, saved
     return out
 
@@ -286,7 +312,7 @@ def run_native(args):
     table_t, _ = om.build_brick_table(spec.aabb, spec.L, spec.brick, occ)
     table = table_t.cpu().numpy()
     scene = om.scene_from_synth(sc, device=dev, table=table)
-    cams = synth.make_cameras(2)
+    cams = rank_cameras(rank)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -328,12 +354,9 @@ def run_native(args):
         step_ms.append(sum(ms))
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t_step = float(np.mean(step_ms))
+    t_step = max_over_ranks(float(np.mean(step_ms)), dev)
     if ws > 1:
         import torch.distributed as dist
-        t = torch.tensor([t_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
         dist.barrier()
     value = ws * rays_per_step / (t_step * 1e-3) / 1e6
 
