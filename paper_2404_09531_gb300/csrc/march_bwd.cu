@@ -20,6 +20,15 @@
 namespace omerf {
 
 constexpr int kBwdThreads = 128;   // 4 warps per CTA
+#ifndef OMERF_PAIR_FOLD
+#define OMERF_PAIR_FOLD 1  // fold neighbouring lanes that share a whole stencil
+#endif
+#ifndef OMERF_RUN_GRID
+#define OMERF_RUN_GRID 1   // otherwise: grid-corner runs folded over up to 2^1 lanes
+#endif
+#ifndef OMERF_RUN_PLANE
+#define OMERF_RUN_PLANE 1  // and plane-texel runs over up to 2^1 lanes
+#endif
 constexpr int kRow = 101;          // staged floats per ray: x 34, h1 16, h2 16, g1 16, g2 16, g3 3
 constexpr int kOwned = (kMlpParams + 31) / 32;  // weights owned per lane (28)
 
@@ -161,6 +170,60 @@ __device__ __forceinline__ void accumulate_rows(const float* __restrict__ rows, 
   __syncwarp();
 }
 
+// Scatter w * dt to the texel at element offset `off`, first summing runs of
+// neighbouring lanes that hit the same texel (consecutive samples of a ray
+// often share a grid corner or plane texel): lanes [l, l + 2^STEPS) of a run
+// are folded into lane l, so one pair of vector reductions is issued per
+// chunk of the run instead of one per sample.  All 32 lanes must call it.
+template <int STEPS>
+__device__ __forceinline__ void scatter8_runs(float* base, int off, float w, const float dt[8], bool valid,
+                                              int lane) {
+  const int key = valid ? off : -1 - lane;
+  const int kprev = __shfl_up_sync(kFull, key, 1);
+  const unsigned H = __ballot_sync(kFull, lane == 0 || kprev != key);
+  const int runstart = 31 - __clz(H & lanemask_le());
+  const unsigned later = H & ~lanemask_le();
+  const int runend = later ? __ffs(later) - 1 : 32;
+  float v[8];
+#pragma unroll
+  for (int c = 0; c < 8; c++) v[c] = valid ? w * dt[c] : 0.0f;
+#pragma unroll
+  for (int st = 0; st < STEPS; st++) {
+    const int dd = 1 << st;
+    const bool take = lane + dd < runend;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      const float u = __shfl_down_sync(kFull, v[c], dd);
+      if (take) v[c] += u;
+    }
+  }
+  if (valid && ((lane - runstart) & ((1 << STEPS) - 1)) == 0) {
+    float4* q = reinterpret_cast<float4*>(base + off);
+    atomicAdd(q, make_float4(v[0], v[1], v[2], v[3]));
+    atomicAdd(q + 1, make_float4(v[4], v[5], v[6], v[7]));
+  }
+}
+
+// Pair folding by stencil: lanes whose samples share the key (the base grid
+// vertex, or a plane's base texel) share every texel of that stencil, so a
+// lane at an even position of a run of equal keys adds its right neighbour's
+// contribution and the neighbour issues nothing.
+__device__ __forceinline__ void pair_fold_info(int key, int lane, bool& emit, bool& partner) {
+  const int kprev = __shfl_up_sync(kFull, key, 1);
+  const unsigned H = __ballot_sync(kFull, lane == 0 || kprev != key);
+  const int runstart = 31 - __clz(H & lanemask_le());
+  const unsigned later = H & ~lanemask_le();
+  const int runend = later ? __ffs(later) - 1 : 32;
+  emit = ((lane - runstart) & 1) == 0;
+  partner = emit && lane + 1 < runend;
+}
+
+__device__ __forceinline__ void red8(float* base, int off, const float v[8]) {
+  float4* q = reinterpret_cast<float4*>(base + off);
+  atomicAdd(q, make_float4(v[0], v[1], v[2], v[3]));
+  atomicAdd(q + 1, make_float4(v[4], v[5], v[6], v[7]));
+}
+
 __device__ __forceinline__ void scatter8(float* base, int off, float w, const float dt[8]) {
   float4* q = reinterpret_cast<float4*>(base + off);
   atomicAdd(q, make_float4(w * dt[0], w * dt[1], w * dt[2], w * dt[3]));
@@ -244,6 +307,9 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
 #pragma unroll
     for (int c = 0; c < 7; c++) Ai[c] = w * s.x[c];
     seg_sum_scan7(Ai, lane, segstart);
+    float dt[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) dt[c] = 0.0f;
     if (act) {
       const int idx = ws.done[r] + (lane - segstart);
       const bool last = idx == ws.cnt[r] - 1;
@@ -258,7 +324,6 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
       }
       const float dah = last ? Ti * (gx - gT) : Ti * gx - suffix / (1.0f - s.ah);
       const float dsig = dah * s.Mv * (1.0f - s.alpha);
-      float dt[8];
       dt[0] = dsig * s.sigma;
 #pragma unroll
       for (int c = 0; c < 7; c++) dt[c + 1] = w * ws.G[r][c] * s.x[c] * (1.0f - s.x[c]);
@@ -267,19 +332,66 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
         const float dz = (s.branch == 1 ? -2.0f : 2.0f) * s.r * g.inv_eps;
         atomicAdd(a.g_occ + 2 * __float_as_int(qb.z) + (s.branch == 1 ? 0 : 1), dM * dz);
       }
-      if (a.g_grid) {
+    }
+    // gradient scatter (all lanes; inactive lanes contribute nothing)
+#if OMERF_PAIR_FOLD
+    float dtn[8];
 #pragma unroll
-        for (int c = 0; c < 8; c++)
-          if (goff[c] >= 0) scatter8(a.g_grid, goff[c], gw[c], dt);
+    for (int c = 0; c < 8; c++) dtn[c] = __shfl_down_sync(kFull, dt[c], 1);
+    if (a.g_grid) {
+      bool emit, partner;
+      pair_fold_info(act && goff[0] >= 0 ? goff[0] : -1 - lane, lane, emit, partner);
+      float gwn[8];
+#pragma unroll
+      for (int c = 0; c < 8; c++) gwn[c] = __shfl_down_sync(kFull, gw[c], 1);
+      if (act && emit) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+          if (goff[c] < 0) continue;
+          float v[8];
+#pragma unroll
+          for (int ch = 0; ch < 8; ch++) v[ch] = partner ? fmaf(gwn[c], dtn[ch], gw[c] * dt[ch]) : gw[c] * dt[ch];
+          red8(a.g_grid, goff[c], v);
+        }
       }
+    }
+    {
+      float* gp[3] = {a.g_xy, a.g_xz, a.g_yz};
+#pragma unroll
+      for (int q = 0; q < 3; q++) {
+        if (!gp[q]) continue;
+        bool emit, partner;
+        pair_fold_info(act ? poff[4 * q] : -1 - lane, lane, emit, partner);
+        float pwn[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) pwn[c] = __shfl_down_sync(kFull, pw[4 * q + c], 1);
+        if (act && emit) {
+#pragma unroll
+          for (int c = 0; c < 4; c++) {
+            float v[8];
+#pragma unroll
+            for (int ch = 0; ch < 8; ch++)
+              v[ch] = partner ? fmaf(pwn[c], dtn[ch], pw[4 * q + c] * dt[ch]) : pw[4 * q + c] * dt[ch];
+            red8(gp[q], poff[4 * q + c], v);
+          }
+        }
+      }
+    }
+#else
+    if (a.g_grid) {
+#pragma unroll
+      for (int c = 0; c < 8; c++) scatter8_runs<OMERF_RUN_GRID>(a.g_grid, goff[c], gw[c], dt, act && goff[c] >= 0, lane);
+    }
+    {
       float* gp[3] = {a.g_xy, a.g_xz, a.g_yz};
 #pragma unroll
       for (int q = 0; q < 3; q++) {
         if (!gp[q]) continue;
 #pragma unroll
-        for (int c = 0; c < 4; c++) scatter8(gp[q], poff[4 * q + c], pw[4 * q + c], dt);
+        for (int c = 0; c < 4; c++) scatter8_runs<OMERF_RUN_PLANE>(gp[q], poff[4 * q + c], pw[4 * q + c], dt, act, lane);
       }
     }
+#endif
     const int rnext = __shfl_down_sync(kFull, r, 1);
     const bool tail = act && (lane == 31 || rnext != r);
     __syncwarp();
