@@ -23,6 +23,9 @@ constexpr int kBwdThreads = 128;   // 4 warps per CTA
 #ifndef OMERF_PAIR_FOLD
 #define OMERF_PAIR_FOLD 1  // fold neighbouring lanes that share a whole stencil
 #endif
+#ifndef OMERF_FOLD
+#define OMERF_FOLD 3       // lanes folded into one reduction
+#endif
 #ifndef OMERF_RUN_GRID
 #define OMERF_RUN_GRID 1   // otherwise: grid-corner runs folded over up to 2^1 lanes
 #endif
@@ -208,14 +211,14 @@ __device__ __forceinline__ void scatter8_runs(float* base, int off, float w, con
 // vertex, or a plane's base texel) share every texel of that stencil, so a
 // lane at an even position of a run of equal keys adds its right neighbour's
 // contribution and the neighbour issues nothing.
-__device__ __forceinline__ void pair_fold_info(int key, int lane, bool& emit, bool& partner) {
+__device__ __forceinline__ void pair_fold_info(int key, int lane, bool& emit, int& nfold) {
   const int kprev = __shfl_up_sync(kFull, key, 1);
   const unsigned H = __ballot_sync(kFull, lane == 0 || kprev != key);
   const int runstart = 31 - __clz(H & lanemask_le());
   const unsigned later = H & ~lanemask_le();
   const int runend = later ? __ffs(later) - 1 : 32;
-  emit = ((lane - runstart) & 1) == 0;
-  partner = emit && lane + 1 < runend;
+  emit = ((lane - runstart) % OMERF_FOLD) == 0;
+  nfold = emit ? min(OMERF_FOLD, runend - lane) : 0;  // lanes [lane, lane + nfold) share the stencil
 }
 
 __device__ __forceinline__ void red8(float* base, int off, const float v[8]) {
@@ -335,24 +338,29 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
     }
     // gradient scatter (all lanes; inactive lanes contribute nothing)
 #if OMERF_PAIR_FOLD
-    float dtn[8];
+    // neighbours' dL/dt and weights, lanes +1 .. +OMERF_FOLD-1
+    float dtn[OMERF_FOLD - 1][8];
 #pragma unroll
-    for (int c = 0; c < 8; c++) dtn[c] = __shfl_down_sync(kFull, dt[c], 1);
+    for (int j = 1; j < OMERF_FOLD; j++)
+#pragma unroll
+      for (int c = 0; c < 8; c++) dtn[j - 1][c] = __shfl_down_sync(kFull, dt[c], j);
     if (a.g_grid) {
-      bool emit, partner;
-      pair_fold_info(act && goff[0] >= 0 ? goff[0] : -1 - lane, lane, emit, partner);
-      float gwn[8];
+      bool emit;
+      int nfold;
+      pair_fold_info(act && goff[0] >= 0 ? goff[0] : -1 - lane, lane, emit, nfold);
 #pragma unroll
-      for (int c = 0; c < 8; c++) gwn[c] = __shfl_down_sync(kFull, gw[c], 1);
-      if (act && emit) {
+      for (int c = 0; c < 8; c++) {
+        float v[8];
 #pragma unroll
-        for (int c = 0; c < 8; c++) {
-          if (goff[c] < 0) continue;
-          float v[8];
+        for (int ch = 0; ch < 8; ch++) v[ch] = gw[c] * dt[ch];
 #pragma unroll
-          for (int ch = 0; ch < 8; ch++) v[ch] = partner ? fmaf(gwn[c], dtn[ch], gw[c] * dt[ch]) : gw[c] * dt[ch];
-          red8(a.g_grid, goff[c], v);
+        for (int j = 1; j < OMERF_FOLD; j++) {
+          const float wn = __shfl_down_sync(kFull, gw[c], j);
+          if (j < nfold)
+#pragma unroll
+            for (int ch = 0; ch < 8; ch++) v[ch] = fmaf(wn, dtn[j - 1][ch], v[ch]);
         }
+        if (act && emit && goff[c] >= 0) red8(a.g_grid, goff[c], v);
       }
     }
     {
@@ -360,20 +368,22 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
 #pragma unroll
       for (int q = 0; q < 3; q++) {
         if (!gp[q]) continue;
-        bool emit, partner;
-        pair_fold_info(act ? poff[4 * q] : -1 - lane, lane, emit, partner);
-        float pwn[4];
+        bool emit;
+        int nfold;
+        pair_fold_info(act ? poff[4 * q] : -1 - lane, lane, emit, nfold);
 #pragma unroll
-        for (int c = 0; c < 4; c++) pwn[c] = __shfl_down_sync(kFull, pw[4 * q + c], 1);
-        if (act && emit) {
+        for (int c = 0; c < 4; c++) {
+          float v[8];
 #pragma unroll
-          for (int c = 0; c < 4; c++) {
-            float v[8];
+          for (int ch = 0; ch < 8; ch++) v[ch] = pw[4 * q + c] * dt[ch];
 #pragma unroll
-            for (int ch = 0; ch < 8; ch++)
-              v[ch] = partner ? fmaf(pwn[c], dtn[ch], pw[4 * q + c] * dt[ch]) : pw[4 * q + c] * dt[ch];
-            red8(gp[q], poff[4 * q + c], v);
+          for (int j = 1; j < OMERF_FOLD; j++) {
+            const float wn = __shfl_down_sync(kFull, pw[4 * q + c], j);
+            if (j < nfold)
+#pragma unroll
+              for (int ch = 0; ch < 8; ch++) v[ch] = fmaf(wn, dtn[j - 1][ch], v[ch]);
           }
+          if (act && emit) red8(gp[q], poff[4 * q + c], v);
         }
       }
     }
