@@ -227,3 +227,33 @@ def test_config4_fp32_full_size_sampled_pixels():
     idx = np.arange(0, rays.shape[0], 127)
     ref = oracle.render(oracle_scene_for(sc, table=table, pool=pool), rays[idx])
     compare_render(rgb[idx], cnt[idx], ref, what="config 4 fp32")
+
+
+def test_scene_update_after_occupancy_change():
+    """Changing occ in place and calling update() gives the render of a fresh
+    scene built on the new occupancy plane (hulls and culling grid rebuilt)."""
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    cam = synth.make_cameras(1)[0]
+    occ2 = sc["occ"].copy()
+    occ2[..., 0] -= 0.02
+    occ2[..., 1] += 0.05
+    occ2[:8, :8] = [0.5, -0.5]  # empty a corner of the plane
+    scene.occ.copy_(torch.as_tensor(occ2))
+    scene.update()
+    rgb, cnt = _render_np(scene, camera=cam)
+    fresh = gpu_scene(dict(sc, occ=occ2))
+    rgb2, cnt2 = _render_np(fresh, camera=cam)
+    np.testing.assert_array_equal(cnt, cnt2)
+    np.testing.assert_array_equal(rgb, rgb2)
+    ref = oracle.render(oracle.OracleScene(dict(sc, occ=occ2)), oracle.camera_rays(cam))
+    compare_render(rgb, cnt, ref, what="updated occupancy")
+
+
+def test_sync_is_bounded():
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    om.render(scene, camera=synth.make_cameras(1)[0])
+    om.sync(timeout_ms=60000)
+    lib = om.lib()
+    assert lib.omerf_sync(None, 0) in (0, -5)  # an idle or busy stream: done or timed out, never blocks

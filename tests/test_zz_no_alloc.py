@@ -74,3 +74,12 @@ def test_rejects_an_occupancy_plane_beyond_the_scratch():
                                   ctypes.c_void_p(rgb.data_ptr()), None, None)
     assert rc == -2
     assert b"no-allocation render reserves" in lib.omerf_last_error()
+
+
+def test_bf16_brick_scene_matches_the_regular_render():
+    sc = synth.make_scene(4)
+    scene = gpu_scene(sc)
+    cam = synth.make_cameras(4)[2]
+    ref = om.render(scene, camera=cam)
+    for call in range(2):
+        _check_same(ref, om.render_noalloc(scene, camera=cam, count=torch.empty_like(ref[1])), f"bf16 call {call}")
