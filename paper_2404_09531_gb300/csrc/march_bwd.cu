@@ -53,89 +53,106 @@ struct BwdArgs {
   unsigned* counter;
 };
 
-// Deferred MLP forward for one lane's ray, writing the staged row
-// (x, h1 = relu(a1), h2 = relu(a2)) to shared memory; returns y.  Output
-// units are produced one at a time (outer loops not unrolled) so that only
-// one layer input lives in registers.
+// Transposed copies of W3, W2 and the first 7 columns of W1 (the weights the
+// backward reads column-wise), 16-byte aligned rows.
+constexpr int kT3 = 0, kT2 = 64, kT1 = 320, kSmemT = 432;
+
+__device__ __forceinline__ void load_mlp_transposed(const float* __restrict__ gw, float* __restrict__ st) {
+  for (int i = threadIdx.x; i < kSmemT; i += blockDim.x) {
+    float v = 0.0f;
+    if (i < kT2) {
+      const int r = i >> 2, c = i & 3;  // W3T[r][c] = W3[c][r], c < 3
+      v = c < 3 ? gw[kOffW3 + c * 16 + r] : 0.0f;
+    } else if (i < kT1) {
+      const int r = (i - kT2) >> 4, c = (i - kT2) & 15;  // W2T[r][c] = W2[c][r]
+      v = gw[kOffW2 + c * 16 + r];
+    } else {
+      const int r = (i - kT1) >> 4, c = (i - kT1) & 15;  // W1T[r][c] = W1[c][r], r < 7
+      v = gw[kOffW1 + c * 34 + r];
+    }
+    st[i] = v;
+  }
+}
+
+// Deferred MLP forward for one lane's ray from the padded weights, writing
+// the staged row (x, h1 = relu(a1), h2 = relu(a2)); returns y.
 __device__ __forceinline__ void mlp_forward_row(const float* __restrict__ W, const float F[7], const float d[3],
                                                 float* __restrict__ row, float y[3]) {
-  {
-    float x[34];
+  float x[36];
 #pragma unroll
-    for (int i = 0; i < 7; i++) x[i] = F[i];
-    view_encoding(d, x + 7);
+  for (int i = 0; i < 7; i++) x[i] = F[i];
+  view_encoding(d, x + 7);
+  x[34] = 0.0f;
+  x[35] = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 34; i++) row[i] = x[i];
-#pragma unroll 1
-    for (int j = 0; j < 16; j++) {
-      float a = W[kOffB1 + j];
+  for (int i = 0; i < 34; i++) row[i] = x[i];
+  float h1[16];
 #pragma unroll
-      for (int i = 0; i < 34; i++) a = fmaf(W[kOffW1 + j * 34 + i], x[i], a);
-      row[34 + j] = fmaxf(a, 0.0f);
-    }
-  }
-  {
-    float h1[16];
+  for (int j = 0; j < 16; j++) {
+    const float4* w = reinterpret_cast<const float4*>(W + kSW1 + 36 * j);
+    float a = W[kSB1 + j];
 #pragma unroll
-    for (int i = 0; i < 16; i++) h1[i] = row[34 + i];
-#pragma unroll 1
-    for (int j = 0; j < 16; j++) {
-      float a = W[kOffB2 + j];
-#pragma unroll
-      for (int i = 0; i < 16; i++) a = fmaf(W[kOffW2 + j * 16 + i], h1[i], a);
-      row[50 + j] = fmaxf(a, 0.0f);
-    }
+    for (int q = 0; q < 9; q++) a = dot4(w[q], x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3], a);
+    h1[j] = fmaxf(a, 0.0f);
+    row[34 + j] = h1[j];
   }
   float h2[16];
 #pragma unroll
-  for (int i = 0; i < 16; i++) h2[i] = row[50 + i];
+  for (int j = 0; j < 16; j++) {
+    const float4* w = reinterpret_cast<const float4*>(W + kSW2 + 16 * j);
+    float a = W[kSB2 + j];
+#pragma unroll
+    for (int q = 0; q < 4; q++) a = dot4(w[q], h1[4 * q], h1[4 * q + 1], h1[4 * q + 2], h1[4 * q + 3], a);
+    h2[j] = fmaxf(a, 0.0f);
+    row[50 + j] = h2[j];
+  }
 #pragma unroll
   for (int j = 0; j < 3; j++) {
-    float a = W[kOffB3 + j];
+    const float4* w = reinterpret_cast<const float4*>(W + kSW3 + 16 * j);
+    float a = W[kSB3 + j];
 #pragma unroll
-    for (int i = 0; i < 16; i++) a = fmaf(W[kOffW3 + j * 16 + i], h2[i], a);
+    for (int q = 0; q < 4; q++) a = dot4(w[q], h2[4 * q], h2[4 * q + 1], h2[4 * q + 2], h2[4 * q + 3], a);
     y[j] = sigmoidf_(a);
   }
 }
 
-// Backprop gy through the staged evaluation: writes the layer deltas
-// (g1, g2, g3) into the row and adds the feature-input gradient into gF.
-// A ReLU unit is active iff its staged output is positive.
-__device__ __forceinline__ void mlp_backward_row(const float* __restrict__ W, float* __restrict__ row,
+// Backprop gy through the staged evaluation with the transposed weights:
+// writes the layer deltas (g1, g2, g3) into the row and adds the
+// feature-input gradient into gF.  A ReLU unit is active iff its staged
+// output is positive.
+__device__ __forceinline__ void mlp_backward_row(const float* __restrict__ WT, float* __restrict__ row,
                                                  const float y[3], const float gy[3], float gF[7]) {
-  float g3[3];
+  float g3[4];
 #pragma unroll
   for (int j = 0; j < 3; j++) {
     g3[j] = gy[j] * y[j] * (1.0f - y[j]);
     row[98 + j] = g3[j];
   }
-#pragma unroll 1
+  g3[3] = 0.0f;
+  float g2[16];
+#pragma unroll
   for (int i = 0; i < 16; i++) {
-    float a = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 3; j++) a = fmaf(W[kOffW3 + j * 16 + i], g3[j], a);
-    row[82 + i] = row[50 + i] > 0.0f ? a : 0.0f;
-  }
-  {
-    float g2[16];
-#pragma unroll
-    for (int j = 0; j < 16; j++) g2[j] = row[82 + j];
-#pragma unroll 1
-    for (int i = 0; i < 16; i++) {
-      float a = 0.0f;
-#pragma unroll
-      for (int j = 0; j < 16; j++) a = fmaf(W[kOffW2 + j * 16 + i], g2[j], a);
-      row[66 + i] = row[34 + i] > 0.0f ? a : 0.0f;
-    }
+    const float4 w = *reinterpret_cast<const float4*>(WT + kT3 + 4 * i);
+    const float a = dot4(w, g3[0], g3[1], g3[2], g3[3], 0.0f);
+    g2[i] = row[50 + i] > 0.0f ? a : 0.0f;
+    row[82 + i] = g2[i];
   }
   float g1[16];
 #pragma unroll
-  for (int j = 0; j < 16; j++) g1[j] = row[66 + j];
-#pragma unroll
-  for (int i = 0; i < 7; i++) {
+  for (int i = 0; i < 16; i++) {
+    const float4* w = reinterpret_cast<const float4*>(WT + kT2 + 16 * i);
     float a = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 16; j++) a = fmaf(W[kOffW1 + j * 34 + i], g1[j], a);
+    for (int q = 0; q < 4; q++) a = dot4(w[q], g2[4 * q], g2[4 * q + 1], g2[4 * q + 2], g2[4 * q + 3], a);
+    g1[i] = row[34 + i] > 0.0f ? a : 0.0f;
+    row[66 + i] = g1[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 7; i++) {
+    const float4* w = reinterpret_cast<const float4*>(WT + kT1 + 16 * i);
+    float a = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; q++) a = dot4(w[q], g1[4 * q], g1[4 * q + 1], g1[4 * q + 2], g1[4 * q + 3], a);
     gF[i] += a;
   }
 }
@@ -420,11 +437,14 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
 __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, const BwdArgs a) {
   extern __shared__ float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* sW = smem;                                   // 884: MLP weights
-  float* sDW = smem + 884 + warp * 884;               // 884 per warp: weight-gradient sums
-  float* rows = smem + 884 * (1 + kBwdThreads / 32) + warp * 32 * kRow;
-  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sW[i] = g.mlp[i];
-  for (int i = threadIdx.x; i < 884 * (kBwdThreads / 32); i += blockDim.x) smem[884 + i] = 0.0f;
+  float* sW = smem;                                   // padded MLP weights
+  float* sWT = smem + kSmemMlp;                       // transposed weights for the backward
+  float* sDWall = smem + kSmemMlp + kSmemT;           // 884 per warp: weight-gradient sums
+  float* sDW = sDWall + warp * 884;
+  float* rows = sDWall + 884 * (kBwdThreads / 32) + warp * 32 * kRow;
+  load_mlp_padded(g.mlp, sW);
+  load_mlp_transposed(g.mlp, sWT);
+  for (int i = threadIdx.x; i < 884 * (kBwdThreads / 32); i += blockDim.x) sDWall[i] = 0.0f;
   __syncthreads();
   const float gs = a.grad_scale ? __ldg(a.grad_scale) : 1.0f;
   const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
@@ -478,7 +498,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
           gys[j] = gs * a.lam_smooth * 2.0f * S * (ys[j] - yd[j]);
           gyd[j] -= gys[j];
         }
-        mlp_backward_row(sW, row, ys, gys, gF);
+        mlp_backward_row(sWT, row, ys, gys, gF);
       } else {
         zero_row(row);
       }
@@ -487,7 +507,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
     if (live) {
       float y[3];
       mlp_forward_row(sW, F, d, row, y);
-      mlp_backward_row(sW, row, y, gyd, gF);
+      mlp_backward_row(sWT, row, y, gyd, gF);
     } else {
       zero_row(row);
     }
@@ -506,7 +526,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
   if (a.g_mlp) {
     for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
       float v = 0.0f;
-      for (int w = 0; w < kBwdThreads / 32; w++) v += smem[884 + w * 884 + i];
+      for (int w = 0; w < kBwdThreads / 32; w++) v += sDWall[w * 884 + i];
       atomicAdd(a.g_mlp + i, v);
     }
   }
@@ -574,7 +594,7 @@ static cudaError_t launch_bwd_variant(const omerf_scene* s, const BwdArgs& a, cu
 }
 
 static cudaError_t launch_mlp_bwd(const omerf_scene* s, const BwdArgs& a, cudaStream_t stream) {
-  const size_t smem = (size_t)(884 * (1 + kBwdThreads / 32) + (kBwdThreads / 32) * 32 * kRow) * sizeof(float);
+  const size_t smem = (size_t)(kSmemMlp + kSmemT + 884 * (kBwdThreads / 32) + (kBwdThreads / 32) * 32 * kRow) * sizeof(float);
   static int blocks[64] = {0};
   const int dev = s->device & 63;
   if (blocks[dev] == 0) {
