@@ -218,6 +218,37 @@ omerf_status omerf_train_step(const omerf_scene *scene, const float *rays, const
                               void *saved, float *loss, float *g_grid, float *g_xy, float *g_xz,
                               float *g_yz, float *g_occ, float *g_mlp, void *stream);
 
+/* One parameter group of an Adam step: float32 master values, gradient and
+ * moments (device, n values each, updated in place; moments start at zero),
+ * an optional bfloat16 copy written after the update (the feature tensor a
+ * BF16 scene renders from), and the group's learning rate. */
+typedef struct {
+    float *param;
+    const float *grad;
+    float *m;
+    float *v;
+    void *shadow_bf16;  /* device bfloat16 [n] or NULL */
+    int64_t n;
+    float lr;
+} omerf_adam_group;
+
+/* Fused Adam step over up to 8 groups in one launch (appendix A trains with
+ * Adam, beta1 = 0.9, beta2 = 0.99, eps = 1e-15; Kingma and Ba's update with
+ * bias correction): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).  step >= 1
+ * counts from 1.  After changing the occupancy plane call omerf_scene_update. */
+omerf_status omerf_adam_step(const omerf_adam_group *groups, int32_t n_groups, float beta1, float beta2,
+                             float eps, int64_t step, void *stream);
+
+/* Learning-rate decay of appendix A: lr0 at step 0 to lr1 at step total,
+ * exponential in between (1e-2 -> 1e-3 for features and MLP, 5e-5 -> 1e-5
+ * for the occupancy plane).  Host-only. */
+float omerf_lr_exponential(float lr0, float lr1, int64_t step, int64_t total);
+
+/* Occupancy-loss weight lambda_7 of appendix A: 0 before iteration 10,000,
+ * then 1e-4 multiplied by 1.5 every 2,000 iterations, at most 0.2.  Host-only. */
+float omerf_lambda_occ(int64_t step);
+
 /* Wait for `stream` with a bounded host-side poll; returns OMERF_ETIMEOUT
  * after timeout_ms milliseconds (< 0 waits without limit), OMERF_ECUDA if
  * the stream reported an error. */

@@ -9,9 +9,13 @@ from .binding import (  # noqa: F401
     OmerfError,
     Scene,
     TrainStep,
+    Trainer,
+    adam_step,
     build_brick_table,
     camera_struct,
+    lambda_occ,
     lib,
+    lr_exponential,
     ray_interval,
     render,
     render_noalloc,
@@ -24,6 +28,6 @@ from .binding import (  # noqa: F401
 )
 
 __all__ = [
-    "OmerfError", "Scene", "TrainStep", "build_brick_table", "camera_struct", "lib", "ray_interval", "render", "render_noalloc",
+    "OmerfError", "Scene", "TrainStep", "Trainer", "adam_step", "build_brick_table", "lambda_occ", "lr_exponential", "camera_struct", "lib", "ray_interval", "render", "render_noalloc",
     "saved_bytes_per_ray", "scene_from_synth", "sync", "train_bwd", "train_fwd", "train_step",
 ]

@@ -72,6 +72,9 @@ SIGNATURES = {
     "omerf_train_fwd": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P]),
     "omerf_train_bwd": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "omerf_train_step": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "omerf_adam_step": (ctypes.c_int, [_P, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, _L, _P]),
+    "omerf_lr_exponential": (ctypes.c_float, [ctypes.c_float, ctypes.c_float, _L, _L]),
+    "omerf_lambda_occ": (ctypes.c_float, [_L]),
     "omerf_sync": (ctypes.c_int, [_P, _I]),
     "omerf_last_error": (ctypes.c_char_p, []),
 }
@@ -407,6 +410,40 @@ def train_step(scene, rays, target, smooth_dirs=None, lam=(1.0, 1e-2, 0.0), grad
     return {"loss": loss, "grads": grads, "saved": saved}
 
 
+class _AdamGroup(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("shadow_bf16", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("lr", ctypes.c_float)]
+
+
+def adam_step(groups, step, beta1=0.9, beta2=0.99, eps=1e-15, stream=None):
+    """Fused Adam step (appendix A).  groups: list of dicts with float32 device
+    tensors param, grad, m, v (same size), a learning rate lr and an optional
+    bfloat16 tensor shadow that receives the updated values."""
+    arr = (_AdamGroup * len(groups))()
+    for i, gr in enumerate(groups):
+        for k in ("param", "grad", "m", "v"):
+            t = gr[k]
+            _require_cuda(t, k)
+            if t.dtype != torch.float32 or t.numel() != gr["param"].numel():
+                raise OmerfError(f"adam group {i}: {k} must be float32 with the param's size")
+        sh = gr.get("shadow")
+        if sh is not None and (sh.dtype != torch.bfloat16 or sh.numel() != gr["param"].numel()):
+            raise OmerfError(f"adam group {i}: shadow must be bfloat16 with the param's size")
+        arr[i] = _AdamGroup(gr["param"].data_ptr(), gr["grad"].data_ptr(), gr["m"].data_ptr(), gr["v"].data_ptr(),
+                            sh.data_ptr() if sh is not None else None, gr["param"].numel(), float(gr["lr"]))
+    _check(lib().omerf_adam_step(arr, len(groups), float(beta1), float(beta2), float(eps), int(step),
+                                 _stream(stream)), "omerf_adam_step")
+
+
+def lr_exponential(lr0, lr1, step, total):
+    return float(lib().omerf_lr_exponential(float(lr0), float(lr1), int(step), int(total)))
+
+
+def lambda_occ(step):
+    return float(lib().omerf_lambda_occ(int(step)))
+
+
 def sync(stream=None, timeout_ms=-1):
     """Bounded wait for a stream (raises OmerfError on timeout or CUDA error)."""
     _check(lib().omerf_sync(_stream(stream), int(timeout_ms)), "omerf_sync")
@@ -443,3 +480,55 @@ class TrainStep(torch.autograd.Function):
 
         return (None, None, None, None, None, cast("grid"), cast("p_xy"), cast("p_xz"), cast("p_yz"),
                 g["occ"], g["mlp"])
+
+
+class Trainer:
+    """The training loop of appendix A over a scene: one fused forward +
+    backward (train_step), one fused Adam step over features, occupancy plane
+    and MLP with exponentially decaying learning rates, the lambda_7 schedule,
+    and a hull update after the occupancy plane moved.  For a BF16 scene the
+    optimiser keeps FP32 master copies and writes the rounded features back
+    into the scene's tensors.
+    """
+
+    def __init__(self, scene: Scene, total_steps=80000, lr=(1e-2, 1e-3), lr_occ=(5e-5, 1e-5), lam_rgb=1.0,
+                 lam_smooth=0.1, lam_occ=None, betas=(0.9, 0.99), eps=1e-15):
+        self.scene = scene
+        self.total = int(total_steps)
+        self.lr, self.lr_occ = lr, lr_occ
+        self.lam_rgb, self.lam_smooth, self.lam_occ = lam_rgb, lam_smooth, lam_occ
+        self.betas, self.eps = betas, eps
+        self.step_no = 0
+        self.grads = _zero_grads(scene)
+        self.master, self.shadow = {}, {}
+        for k in ("grid", "p_xy", "p_xz", "p_yz", "occ", "mlp"):
+            t = getattr(scene, k)
+            if t.dtype == torch.float32:
+                self.master[k], self.shadow[k] = t, None
+            else:
+                self.master[k], self.shadow[k] = t.float().contiguous(), t
+        self.moments = {k: (torch.zeros_like(v), torch.zeros_like(v)) for k, v in self.master.items()}
+        self.saved = None
+
+    def step(self, rays, target, smooth_dirs=None):
+        lam7 = lambda_occ(self.step_no) if self.lam_occ is None else self.lam_occ
+        lam = (self.lam_rgb, self.lam_smooth, lam7)
+        for g in self.grads.values():
+            g.zero_()
+        n = int(torch.as_tensor(rays).shape[0])
+        if self.saved is None or self.saved.numel() < n * saved_bytes_per_ray() // 4:
+            self.saved = torch.empty(max(n, 1) * saved_bytes_per_ray() // 4, dtype=torch.float32,
+                                     device=self.scene.device)
+        res = train_step(self.scene, rays, target, smooth_dirs, lam=lam, grads=self.grads, saved=self.saved)
+        lr = lr_exponential(self.lr[0], self.lr[1], self.step_no, self.total)
+        lr_o = lr_exponential(self.lr_occ[0], self.lr_occ[1], self.step_no, self.total)
+        groups = []
+        for k, p in self.master.items():
+            m, v = self.moments[k]
+            groups.append({"param": p.view(-1), "grad": self.grads[k].view(-1), "m": m.view(-1), "v": v.view(-1),
+                           "lr": lr_o if k == "occ" else lr,
+                           "shadow": None if self.shadow[k] is None else self.shadow[k].view(-1)})
+        self.step_no += 1
+        adam_step(groups, self.step_no, beta1=self.betas[0], beta2=self.betas[1], eps=self.eps)
+        self.scene.update()
+        return res["loss"]

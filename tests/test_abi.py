@@ -76,3 +76,11 @@ def test_host_validation_without_gpu(lib):
                                        ctypes.c_void_p(4096), None) == -1
     assert lib.omerf_render(None, None, None, 10, None, None, None) == -1
     assert lib.omerf_saved_bytes_per_ray() == 80
+
+
+def test_host_schedules_match_reference(lib):
+    from oracle import adam
+    for step in (0, 1000, 40000, 80000):
+        assert lib.omerf_lr_exponential(5e-5, 1e-5, step, 80000) == pytest.approx(adam.lr_exponential(5e-5, 1e-5, step, 80000), rel=1e-6)
+    for step in (0, 9999, 10000, 14000, 10 ** 8):
+        assert lib.omerf_lambda_occ(step) == pytest.approx(adam.lambda_occ(step), rel=1e-6)

@@ -1,0 +1,62 @@
+"""GPU parity of the fused Adam step (appendix A optimiser) against the FP64
+reference in oracle/adam.py, and a short end-to-end training loop."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import adam as ref_adam
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+import paper_2404_09531_gb300 as om  # noqa: E402
+
+
+def test_adam_matches_reference_over_steps():
+    rng = np.random.default_rng(7)
+    sizes = [1000, 33, 4097]
+    lrs = [1e-2, 5e-5, 3e-3]
+    p_ref = [rng.normal(size=n) for n in sizes]
+    m_ref = [np.zeros(n) for n in sizes]
+    v_ref = [np.zeros(n) for n in sizes]
+    p = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in p_ref]
+    p_ref = [x.astype(np.float32).astype(np.float64) for x in p_ref]
+    m = [torch.zeros(n, device="cuda") for n in sizes]
+    v = [torch.zeros(n, device="cuda") for n in sizes]
+    shadow = torch.empty(sizes[2], dtype=torch.bfloat16, device="cuda")
+    for step in range(1, 9):
+        grads = [rng.normal(size=n).astype(np.float32) for n in sizes]
+        gd = [torch.tensor(g, device="cuda") for g in grads]
+        groups = [{"param": p[i], "grad": gd[i], "m": m[i], "v": v[i], "lr": lrs[i]} for i in range(3)]
+        groups[2]["shadow"] = shadow
+        om.adam_step(groups, step)
+        for i in range(3):
+            p_ref[i], m_ref[i], v_ref[i] = ref_adam.adam_step(p_ref[i], grads[i], m_ref[i], v_ref[i], lrs[i], step)
+    torch.cuda.synchronize()
+    for i in range(3):
+        np.testing.assert_allclose(p[i].cpu().numpy(), p_ref[i], rtol=0, atol=1e-5 * lrs[i] / 1e-3 + 1e-6)
+        np.testing.assert_allclose(m[i].cpu().numpy(), m_ref[i], rtol=1e-5, atol=1e-7)
+        np.testing.assert_allclose(v[i].cpu().numpy(), v_ref[i], rtol=1e-5, atol=1e-9)
+    np.testing.assert_array_equal(shadow.float().cpu().numpy(), p[2].to(torch.bfloat16).float().cpu().numpy())
+
+
+def test_schedule_functions_match_reference():
+    for step in (0, 5000, 40000, 80000, 90000):
+        assert om.lr_exponential(1e-2, 1e-3, step, 80000) == pytest.approx(ref_adam.lr_exponential(1e-2, 1e-3, step, 80000), rel=1e-6)
+    for step in (0, 9999, 10000, 12000, 30000, 10 ** 6):
+        assert om.lambda_occ(step) == pytest.approx(ref_adam.lambda_occ(step), rel=1e-6)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_training_loop_reduces_the_loss(dtype):
+    sc = synth.make_scene(3)
+    target_scene = synth.perturb_scene(sc, sigma=0.3)
+    batch = synth.make_train_batch(3, 1 << 14, seed=5)
+    target = oracle.render(oracle.OracleScene(target_scene), batch["rays"])["rgb"].astype(np.float32)
+    scene = om.scene_from_synth(sc, device="cuda", feat_dtype=torch.bfloat16 if dtype == "bf16" else torch.float32)
+    tr = om.Trainer(scene, total_steps=200, lam_occ=1e-4)
+    losses = [float(tr.step(batch["rays"], target, batch["smooth_dirs"])[0]) for _ in range(30)]
+    assert losses[-1] < 0.7 * losses[0], losses
+    assert np.all(np.isfinite(losses))
