@@ -9,8 +9,9 @@ Functions follow Oblique-MERF (arXiv 2404.09531):
   train (loss + analytic gradient)                             Eqs. 5, 9-10, 12
   camera_rays                                                  pinhole rays (FP32 rule)
   brick_table                                                  Sec. 4.4 brick allocation
+  sparsity / entropy (loss + analytic gradient)                Eqs. 13, 14 (Sec. 4.3)
 
-Parity status: every function is pinned in tests/test_oracle.py by closed
+Parity status: every function is pinned in tests/test_oracle*.py by closed
 forms, invariants, library routines or brute force (see that file).  No
 function is pinned to a value the paper prints: the paper prints no worked
 example for any synthetic input.
@@ -88,6 +89,10 @@ def _load():
         lib.or_brick_table.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int, P]
         lib.or_ray_weights.restype = ctypes.c_int
         lib.or_ray_weights.argtypes = [P, P, P, P]
+        lib.or_sparsity.restype = ctypes.c_double
+        lib.or_sparsity.argtypes = [P, P, ctypes.c_long, ctypes.c_double, ctypes.c_double, P, P, P, P]
+        lib.or_entropy.restype = ctypes.c_double
+        lib.or_entropy.argtypes = [P, P, ctypes.c_long, ctypes.c_double, ctypes.c_double, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -253,3 +258,35 @@ def brick_table(spec, occ: np.ndarray) -> np.ndarray:
     occ = np.ascontiguousarray(occ, np.float32)
     _load().or_brick_table(_ptr(aabb), _ptr(L), B, _ptr(occ), spec.M, _ptr(table))
     return table
+
+
+def _reg_grads(oscene, want_grad, occ=False):
+    if not want_grad:
+        return {}
+    g = {"grid": np.zeros_like(oscene.grid), "p_xy": np.zeros_like(oscene.pxy),
+         "p_xz": np.zeros_like(oscene.pxz), "p_yz": np.zeros_like(oscene.pyz)}
+    if occ:
+        g["occ"] = np.zeros_like(oscene.occ)
+    return g
+
+
+def sparsity(oscene: OracleScene, points, lam=0.05, grad_scale=1.0, want_grad=True) -> dict:
+    """Eq. 13: lam * mean opacity at the given points [n][3]; FP64 gradient."""
+    pts = np.ascontiguousarray(points, np.float64)
+    g = _reg_grads(oscene, want_grad)
+    d = oscene.desc()
+    loss = _load().or_sparsity(ctypes.byref(d), _ptr(pts), pts.shape[0], float(lam), float(grad_scale),
+                               _ptr(g.get("grid")), _ptr(g.get("p_xy")), _ptr(g.get("p_xz")), _ptr(g.get("p_yz")))
+    return {"loss": float(loss), "grads": g}
+
+
+def entropy(oscene: OracleScene, rays, lam=1e-3, grad_scale=1.0, want_grad=True) -> dict:
+    """Eq. 14: lam * mean over rays of -sum p log p, p = M alpha / sum M alpha."""
+    rays = np.ascontiguousarray(rays, np.float32)
+    g = _reg_grads(oscene, want_grad, occ=True)
+    d = oscene.desc()
+    loss = _load().or_entropy(ctypes.byref(d), _ptr(rays), rays.shape[0], float(lam), float(grad_scale),
+                              _ptr(g.get("grid")), _ptr(g.get("p_xy")), _ptr(g.get("p_xz")), _ptr(g.get("p_yz")),
+                              _ptr(g.get("occ")))
+    return {"loss": float(loss), "grads": g}
+

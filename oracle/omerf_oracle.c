@@ -21,6 +21,8 @@
  *   gradient        reverse mode by hand (textbook back-to-front sweep)
  *   brick table     feature bricks stored where the occupancy plane says
  *                   "occupied" (Sec. 4.4)
+ *   sparsity loss   mean opacity of given points in the occupied space (Eq. 13)
+ *   entropy loss    -sum p log p along top-down rays, p = M alpha / sum M alpha (Eq. 14)
  *
  * Readings of the paper taken here (all also used by the CUDA path):
  *   - the sample lattice is t_k = k * step (k >= 0) from the ray origin; which
@@ -731,3 +733,96 @@ long or_brick_table(const float *aabb, const int32_t *L, int B, const float *occ
             }
     return next;
 }
+
+/* ------------------------------------------------------------------ */
+/* regularisers of Sec. 4.3                                            */
+/* ------------------------------------------------------------------ */
+
+static void scatter_stencil(const or_scene *s, const or_stencil *st, const double dt[NCH], double *g_grid,
+                            double *g_xy, double *g_xz, double *g_yz)
+{
+    if (g_grid)
+        for (int a = 0; a < 8; a++) {
+            if (st->gidx[a] < 0) continue;
+            for (int c = 0; c < NCH; c++) g_grid[st->gidx[a] + c] += st->gw[a] * dt[c];
+        }
+    double *gp[3] = {g_xy, g_xz, g_yz};
+    for (int q = 0; q < 3; q++) {
+        if (!gp[q]) continue;
+        for (int a = 0; a < 4; a++)
+            for (int c = 0; c < NCH; c++) gp[q][st->pidx[q][a] + c] += st->pw[q][a] * dt[c];
+    }
+}
+
+/*
+ * Sparsity loss (Eq. 13): L = lam / n * sum_i alpha(p_i), alpha = 1 -
+ * exp(-tau(p) delta) with delta the lattice step (reading: the opacity a
+ * sample at p would have).  Points [n][3] are given by the caller.
+ * Returns L; gradients (may be NULL) accumulate grad_scale * dL/dparam.
+ */
+double or_sparsity(const or_scene *s, const double *pts, long n, double lam, double grad_scale, double *g_grid,
+                   double *g_xy, double *g_xz, double *g_yz)
+{
+    double acc = 0.0;
+    for (long i = 0; i < n; i++) {
+        or_stencil st;
+        make_stencil(s, pts + 3 * i, &st, NULL);
+        double t[NCH];
+        eval_features(s, &st, t);
+        double sigma = exp(t[0]) * (double)s->step;
+        double alpha = -expm1(-sigma);
+        acc += alpha;
+        double dt[NCH] = {0, 0, 0, 0, 0, 0, 0, 0};
+        dt[0] = grad_scale * lam / (double)n * (1.0 - alpha) * sigma;
+        scatter_stencil(s, &st, dt, g_grid, g_xy, g_xz, g_yz);
+    }
+    return n > 0 ? lam * acc / (double)n : 0.0;
+}
+
+/*
+ * Entropy loss (Eq. 14) over n rays: for each ray, a_i = M_i alpha_i over its
+ * evaluated samples (no early termination; the n_max cap applies), p_i =
+ * a_i / S with S = sum a_i, L_r = -sum p_i log p_i; L = lam / n * sum_r L_r.
+ * Rays with S = 0 contribute 0.  dL_r/da_k = -(log p_k + L_r) / S.
+ * Returns L; gradients (may be NULL) accumulate grad_scale * dL/dparam.
+ */
+double or_entropy(const or_scene *s, const float *rays, long n, double lam, double grad_scale, double *g_grid,
+                  double *g_xy, double *g_xz, double *g_yz, double *g_occ)
+{
+    or_scene s0 = *s;
+    s0.t_thr = 0.0f;
+    or_sample *smp = (or_sample *)malloc(sizeof(or_sample) * (size_t)(s->n_max > 0 ? s->n_max : 1));
+    double total = 0.0;
+    for (long r = 0; r < n; r++) {
+        or_march m;
+        march_ray(&s0, rays + 6 * r, smp, &m);
+        double S = 0.0;
+        for (int i = 0; i < m.count; i++) S += smp[i].ah;
+        if (!(S > 0.0)) continue;
+        double L = 0.0;
+        for (int i = 0; i < m.count; i++) {
+            double p = smp[i].ah / S;
+            if (p > 0.0) L -= p * log(p);
+        }
+        total += L;
+        for (int i = 0; i < m.count; i++) {
+            const or_sample *q = &smp[i];
+            if (!(q->ah > 0.0)) continue;
+            double da = grad_scale * lam / (double)n * (-(log(q->ah / S) + L) / S);
+            double dsig = da * q->Mv * (1.0 - q->alpha);
+            double dM = da * q->alpha;
+            double dt[NCH] = {0, 0, 0, 0, 0, 0, 0, 0};
+            dt[0] = dsig * q->sigma;
+            or_stencil st;
+            make_stencil(&s0, q->p, &st, NULL);
+            scatter_stencil(&s0, &st, dt, g_grid, g_xy, g_xz, g_yz);
+            if (g_occ) {
+                if (q->branch == 1) g_occ[2 * q->cell] += dM * (-2.0 * q->r / (double)s->eps);
+                if (q->branch == 2) g_occ[2 * q->cell + 1] += dM * (2.0 * q->r / (double)s->eps);
+            }
+        }
+    }
+    free(smp);
+    return n > 0 ? lam * total / (double)n : 0.0;
+}
+

@@ -16,5 +16,7 @@ from .scene import (  # noqa: F401
     fill_brick_pool,
     perturb_scene,
     scene_spec,
+    sparsity_points,
+    entropy_rays,
     tiny_scene,
 )

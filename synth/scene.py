@@ -326,6 +326,42 @@ def make_train_batch(cfg: int | SceneSpec, n_rays: int, K: int = 1, seed: int | 
     return {"rays": rays, "smooth_dirs": smooth, "target": target}
 
 
+def sparsity_points(scene: dict, n: int, seed: int | None = None) -> np.ndarray:
+    """Random points in the occupied space (the point set of Eq. 13): a
+    uniformly chosen non-empty occupancy cell, x and y uniform inside it, z
+    uniform in the cell's open interval (z_min, z_max).  float32 [n][3]."""
+    spec = scene["spec"]
+    rng = _rng(spec.cfg if seed is None else seed, 2500)
+    occ = np.asarray(scene["occ"], np.float64).reshape(-1, 2)
+    live = np.flatnonzero(occ[:, 0] < occ[:, 1])
+    pts = np.zeros((n, 3), np.float32)
+    if n == 0 or live.size == 0:
+        return pts
+    x0, x1, y0, y1 = spec.aabb[:4]
+    M = spec.M
+    cell = live[rng.integers(0, live.size, n)]
+    cx, cy = cell // M, cell % M
+    x = x0 + (cx + rng.uniform(0.0, 1.0, n)) * (x1 - x0) / M
+    y = y0 + (cy + rng.uniform(0.0, 1.0, n)) * (y1 - y0) / M
+    lo, hi = occ[cell, 0], occ[cell, 1]
+    z = lo + rng.uniform(0.02, 0.98, n) * (hi - lo)
+    pts[:, 0], pts[:, 1], pts[:, 2] = x, y, z
+    return pts
+
+
+def entropy_rays(scene: dict, n: int, seed: int | None = None, tilt: float = 0.2) -> np.ndarray:
+    """Rays from high altitude to the ground (the ray set of Eq. 14): origins
+    uniform over the box footprint, half the box height above its top,
+    directions -z tilted by up to `tilt` (tangent) in x and y.  float32 [n][6]."""
+    spec = scene["spec"]
+    rng = _rng(spec.cfg if seed is None else seed, 3000)
+    x0, x1, y0, y1, z0, z1 = spec.aabb
+    o = np.stack([rng.uniform(x0, x1, n), rng.uniform(y0, y1, n), np.full(n, z1 + 0.5 * (z1 - z0))], 1)
+    d = np.stack([rng.uniform(-tilt, tilt, n), rng.uniform(-tilt, tilt, n), -np.ones(n)], 1)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return np.concatenate([o, d], 1).astype(np.float32)
+
+
 def tiny_scene(seed: int = 0, L=(4, 4, 4), R=(4, 4, 4), M=2, n_rays=4, brick=0,
                occ_margin=0.35, step=1.0 / 16, eps=0.1) -> dict:
     """A few-parameter scene for finite-difference and hand-checked tests."""
