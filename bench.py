@@ -38,7 +38,7 @@ BYTES_PER_RAY_RENDER = 12 + 4                          # rgb + count written
 # (one 1920x1080 frame of march_fwd_kernel<float, sparse, render>), from the ncu
 # capture summarised in profiles/march_fwd_render1080_sparse_f32.md; set to None
 # whenever that kernel changes until it is captured again.
-TRAFFIC_PER_LAUNCH = 53.404416e6 + 6.373376e6
+TRAFFIC_PER_LAUNCH = 53.457664e6 + 5.970432e6
 
 
 def _peaks():
@@ -406,9 +406,27 @@ def run_native(args):
 
     # the full optimisation step of appendix A: fwd + bwd, fused Adam over
     # features, occupancy plane and MLP (one launch), hull update
+    # (with the paper's regulariser batches: 2^14 sparsity points, 2^10 entropy rays)
+    pts_d = torch.as_tensor(synth.sparsity_points(tsc, 1 << 14)).to(dev)
+    erays_d = torch.as_tensor(synth.entropy_rays(tsc, 1 << 10)).to(dev)
+    reg_grads = om.binding._zero_grads(tscene)
+    reg_loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    sp_ms, en_ms = [], []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        om.sparsity_loss(tscene, pts_d, lam=0.05, grads=reg_grads, loss=reg_loss)
+        b.record(stream)
+        om.entropy_loss(tscene, erays_d, lam=1e-3, grads=reg_grads, loss=reg_loss)
+        c.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            sp_ms.append(a.elapsed_time(b))
+            en_ms.append(b.elapsed_time(c))
     trainer = om.Trainer(tscene, total_steps=80000, lam_occ=1e-4)
     for _ in range(args.warmup):
-        trainer.step(rays_d, target, dirs_d)
+        trainer.step(rays_d, target, dirs_d, sparsity_points=pts_d, entropy_rays=erays_d)
     loop_ms, adam_ms = [], []
     groups = [{"param": p.view(-1), "grad": trainer.grads[k].view(-1), "m": trainer.moments[k][0].view(-1),
                "v": trainer.moments[k][1].view(-1), "lr": 1e-3} for k, p in trainer.master.items()]
@@ -417,7 +435,7 @@ def run_native(args):
         flush.fill_(1.0)
         a, b, c, e = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         a.record(stream)
-        trainer.step(rays_d, target, dirs_d)
+        trainer.step(rays_d, target, dirs_d, sparsity_points=pts_d, entropy_rays=erays_d)
         b.record(stream)
         c.record(stream)
         om.adam_step(groups, 1000)
@@ -461,7 +479,12 @@ def run_native(args):
                   "unit": "Mrays/s", "ms_per_step": t_train, "rays_per_step": 1 << 18, "loss": loss,
                   "with_adam": {"value": (1 << 18) / (t_loop * 1e-3) / 1e6, "unit": "Mrays/s",
                                 "ms_per_step": t_loop,
-                                "note": "fwd + bwd + fused Adam (lr decay, lambda_7 fixed at 1e-4) + hull update"},
+                                "note": "fwd + bwd + sparsity and entropy terms + fused Adam (lr decay, "
+                                        "lambda_7 fixed at 1e-4) + hull update; the scene evolves under the "
+                                        "optimiser, so its sample counts differ from the fwd+bwd line"},
+                  "regularizers": {"sparsity_us": float(np.mean(sp_ms)) * 1e3, "points": 1 << 14,
+                                   "entropy_us": float(np.mean(en_ms)) * 1e3, "rays": 1 << 10,
+                                   "note": "Eqs. 13-14, loss + gradient, one launch each"},
                   "adam": {"us": t_adam * 1e3, "params": n_params,
                            "achieved_gbs": 28.0 * n_params / (t_adam * 1e-3) / 1e9,
                            "note": "28 B per parameter (read p, g, m, v; write p, m, v)"}},

@@ -185,7 +185,7 @@ omerf_status omerf_render_noalloc(const omerf_scene_desc *desc, const omerf_came
 /* Bytes of per-ray state that omerf_train_fwd writes for omerf_train_bwd. */
 int64_t omerf_saved_bytes_per_ray(void);
 
-/* Training forward (Eqs. 5, 9-10, 12), float32 features only:
+/* Training forward (Eqs. 5, 9-10, 12), float32 or bfloat16 features:
  *   L = lambda[0] * mean_r sqrt(|C_r - C*_r|^2 + 1e-6)
  *     + lambda[1] * mean_r sum_k S(d, s_k) |G(F, s_k/|s_k|) - G(F, d)|^2
  *     + lambda[2] * sum_cells (z_max - z_min)^2
@@ -217,6 +217,33 @@ omerf_status omerf_train_step(const omerf_scene *scene, const float *rays, const
                               const float *smooth_dirs, int64_t n, int32_t K, const float lambda[3],
                               void *saved, float *loss, float *g_grid, float *g_xy, float *g_xz,
                               float *g_yz, float *g_occ, float *g_mlp, void *stream);
+
+/* Sparsity loss (Sec. 4.3, Eq. 13): L = lambda / n * sum_i alpha(p_i) with
+ * alpha = 1 - exp(-tau(p) * step), tau = exp of the density channel of Eq. 2,
+ * over n caller-chosen points (the paper draws them in the occupied space).
+ *   points  device float32 [n][3]
+ *   loss    device float32 [1] or NULL: L is ADDED (+=) to *loss
+ *   g_*     caller-owned float32 gradient buffers shaped like the parameters
+ *           (g_grid like the dense grid or the brick pool), each may be NULL:
+ *           grad_scale * dL/dparam is ADDED; only channel 0 is touched
+ *   grad_scale  device float32 scalar or NULL (1)
+ * Float32 or bfloat16 features.  One kernel launch. */
+omerf_status omerf_sparsity_loss(const omerf_scene *scene, const float *points, int64_t n, float lambda,
+                                 const float *grad_scale, float *loss, float *g_grid, float *g_xy,
+                                 float *g_xz, float *g_yz, void *stream);
+
+/* Entropy loss (Sec. 4.3, Eq. 14) over n rays (the paper casts them from high
+ * altitude towards the ground): for each ray, a_i = M_i alpha_i over its
+ * evaluated samples (the sample rule of Eq. 7 with no early termination, at
+ * most n_max samples), p_i = a_i / sum_j a_j, L_r = -sum_i p_i log p_i;
+ * L = lambda / n * sum_r L_r.  Rays with no sample add nothing.  The gradient
+ * reaches channel 0 of the features and, through the occupancy ramps of
+ * Eq. 6, both z bounds of the occupancy plane (g_occ [M][M][2], 8-byte
+ * aligned).  Arguments otherwise as omerf_sparsity_loss; rays device float32
+ * [n][6] (origin, unit direction).  One kernel launch. */
+omerf_status omerf_entropy_loss(const omerf_scene *scene, const float *rays, int64_t n, float lambda,
+                                const float *grad_scale, float *loss, float *g_grid, float *g_xy,
+                                float *g_xz, float *g_yz, float *g_occ, void *stream);
 
 /* One parameter group of an Adam step: float32 master values, gradient and
  * moments (device, n values each, updated in place; moments start at zero),

@@ -13,6 +13,7 @@ from .binding import (  # noqa: F401
     adam_step,
     build_brick_table,
     camera_struct,
+    entropy_loss,
     lambda_occ,
     lib,
     lr_exponential,
@@ -21,6 +22,7 @@ from .binding import (  # noqa: F401
     render_noalloc,
     saved_bytes_per_ray,
     scene_from_synth,
+    sparsity_loss,
     sync,
     train_bwd,
     train_fwd,
@@ -28,6 +30,7 @@ from .binding import (  # noqa: F401
 )
 
 __all__ = [
-    "OmerfError", "Scene", "TrainStep", "Trainer", "adam_step", "build_brick_table", "lambda_occ", "lr_exponential", "camera_struct", "lib", "ray_interval", "render", "render_noalloc",
-    "saved_bytes_per_ray", "scene_from_synth", "sync", "train_bwd", "train_fwd", "train_step",
+    "OmerfError", "Scene", "TrainStep", "Trainer", "adam_step", "build_brick_table", "camera_struct",
+    "entropy_loss", "lambda_occ", "lib", "lr_exponential", "ray_interval", "render", "render_noalloc",
+    "saved_bytes_per_ray", "scene_from_synth", "sparsity_loss", "sync", "train_bwd", "train_fwd", "train_step",
 ]

@@ -72,6 +72,8 @@ SIGNATURES = {
     "omerf_train_fwd": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P]),
     "omerf_train_bwd": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "omerf_train_step": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "omerf_sparsity_loss": (ctypes.c_int, [_P, _P, _L, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P]),
+    "omerf_entropy_loss": (ctypes.c_int, [_P, _P, _L, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P, _P]),
     "omerf_adam_step": (ctypes.c_int, [_P, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, _L, _P]),
     "omerf_lr_exponential": (ctypes.c_float, [ctypes.c_float, ctypes.c_float, _L, _L]),
     "omerf_lambda_occ": (ctypes.c_float, [_L]),
@@ -410,6 +412,47 @@ def train_step(scene, rays, target, smooth_dirs=None, lam=(1.0, 1e-2, 0.0), grad
     return {"loss": loss, "grads": grads, "saved": saved}
 
 
+def _grad_scale(scene, grad_scale):
+    if grad_scale is None:
+        return None
+    return torch.as_tensor(grad_scale, dtype=torch.float32, device=scene.device).reshape(1).contiguous()
+
+
+def _reg_loss(loss, scene):
+    if loss is None:
+        return torch.zeros(1, dtype=torch.float32, device=scene.device)
+    _require_cuda(loss, "loss")
+    return loss
+
+
+def sparsity_loss(scene, points, lam=0.05, grads=None, loss=None, grad_scale=None, stream=None):
+    """Eq. 13: adds lam * mean alpha over ``points`` [n][3] to ``loss`` (a new
+    [1] tensor when None) and grad_scale * dL/dparam to ``grads`` (a dict as
+    from train_step; None skips the gradient).  Returns the loss tensor."""
+    pts = _dev_f32(points, scene.device)
+    n = int(pts.shape[0]) if pts.numel() else 0
+    loss = _reg_loss(loss, scene)
+    g = grads or {}
+    _check(lib().omerf_sparsity_loss(scene.handle, _ptr(pts), n, float(lam), _ptr(_grad_scale(scene, grad_scale)),
+                                     _ptr(loss), _ptr(g.get("grid")), _ptr(g.get("p_xy")), _ptr(g.get("p_xz")),
+                                     _ptr(g.get("p_yz")), _stream(stream)), "omerf_sparsity_loss")
+    return loss
+
+
+def entropy_loss(scene, rays, lam=1e-3, grads=None, loss=None, grad_scale=None, stream=None):
+    """Eq. 14: adds lam * mean over ``rays`` [n][6] of -sum p log p
+    (p = M alpha / sum M alpha) to ``loss`` and its gradient (features and
+    occupancy plane) to ``grads``.  Returns the loss tensor."""
+    r = _dev_f32(rays, scene.device)
+    n = int(r.shape[0]) if r.numel() else 0
+    loss = _reg_loss(loss, scene)
+    g = grads or {}
+    _check(lib().omerf_entropy_loss(scene.handle, _ptr(r), n, float(lam), _ptr(_grad_scale(scene, grad_scale)),
+                                    _ptr(loss), _ptr(g.get("grid")), _ptr(g.get("p_xy")), _ptr(g.get("p_xz")),
+                                    _ptr(g.get("p_yz")), _ptr(g.get("occ")), _stream(stream)), "omerf_entropy_loss")
+    return loss
+
+
 class _AdamGroup(ctypes.Structure):
     _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
                 ("v", ctypes.c_void_p), ("shadow_bf16", ctypes.c_void_p), ("n", ctypes.c_int64),
@@ -484,7 +527,8 @@ class TrainStep(torch.autograd.Function):
 
 class Trainer:
     """The training loop of appendix A over a scene: one fused forward +
-    backward (train_step), one fused Adam step over features, occupancy plane
+    backward (train_step), the sparsity and entropy terms (Eqs. 13-14) when
+    their point and ray sets are given, one fused Adam step over features, occupancy plane
     and MLP with exponentially decaying learning rates, the lambda_7 schedule,
     and a hull update after the occupancy plane moved.  For a BF16 scene the
     optimiser keeps FP32 master copies and writes the rounded features back
@@ -492,11 +536,13 @@ class Trainer:
     """
 
     def __init__(self, scene: Scene, total_steps=80000, lr=(1e-2, 1e-3), lr_occ=(5e-5, 1e-5), lam_rgb=1.0,
-                 lam_smooth=0.1, lam_occ=None, betas=(0.9, 0.99), eps=1e-15):
+                 lam_smooth=0.1, lam_occ=None, lam_sparsity=0.05, lam_entropy=1e-3, betas=(0.9, 0.99),
+                 eps=1e-15):
         self.scene = scene
         self.total = int(total_steps)
         self.lr, self.lr_occ = lr, lr_occ
         self.lam_rgb, self.lam_smooth, self.lam_occ = lam_rgb, lam_smooth, lam_occ
+        self.lam_sparsity, self.lam_entropy = lam_sparsity, lam_entropy
         self.betas, self.eps = betas, eps
         self.step_no = 0
         self.grads = _zero_grads(scene)
@@ -510,7 +556,10 @@ class Trainer:
         self.moments = {k: (torch.zeros_like(v), torch.zeros_like(v)) for k, v in self.master.items()}
         self.saved = None
 
-    def step(self, rays, target, smooth_dirs=None):
+    def step(self, rays, target, smooth_dirs=None, sparsity_points=None, entropy_rays=None):
+        """One iteration; the optional point and ray sets add the sparsity
+        (Eq. 13) and entropy (Eq. 14) terms to the loss total (slot 0) and the
+        gradients before the Adam step."""
         lam7 = lambda_occ(self.step_no) if self.lam_occ is None else self.lam_occ
         lam = (self.lam_rgb, self.lam_smooth, lam7)
         for g in self.grads.values():
@@ -520,6 +569,11 @@ class Trainer:
             self.saved = torch.empty(max(n, 1) * saved_bytes_per_ray() // 4, dtype=torch.float32,
                                      device=self.scene.device)
         res = train_step(self.scene, rays, target, smooth_dirs, lam=lam, grads=self.grads, saved=self.saved)
+        total = res["loss"][0:1]
+        if sparsity_points is not None and self.lam_sparsity:
+            sparsity_loss(self.scene, sparsity_points, lam=self.lam_sparsity, grads=self.grads, loss=total)
+        if entropy_rays is not None and self.lam_entropy:
+            entropy_loss(self.scene, entropy_rays, lam=self.lam_entropy, grads=self.grads, loss=total)
         lr = lr_exponential(self.lr[0], self.lr[1], self.step_no, self.total)
         lr_o = lr_exponential(self.lr_occ[0], self.lr_occ[1], self.step_no, self.total)
         groups = []

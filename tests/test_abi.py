@@ -76,6 +76,10 @@ def test_host_validation_without_gpu(lib):
                                        ctypes.c_void_p(4096), None) == -1
     assert lib.omerf_render(None, None, None, 10, None, None, None) == -1
     assert lib.omerf_saved_bytes_per_ray() == 80
+    # the regularisers reject a missing scene before touching the device
+    assert lib.omerf_sparsity_loss(None, None, 0, 0.05, None, None, None, None, None, None, None) == -1
+    assert lib.omerf_entropy_loss(None, None, 0, 1e-3, None, None, None, None, None, None, None, None) == -1
+    assert b"NULL scene" in lib.omerf_last_error()
 
 
 def test_host_schedules_match_reference(lib):

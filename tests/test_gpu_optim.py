@@ -60,3 +60,30 @@ def test_training_loop_reduces_the_loss(dtype):
     losses = [float(tr.step(batch["rays"], target, batch["smooth_dirs"])[0]) for _ in range(30)]
     assert losses[-1] < 0.7 * losses[0], losses
     assert np.all(np.isfinite(losses))
+
+
+def test_trainer_adds_the_regularisers_to_loss_and_gradients():
+    """One Trainer step with the sparsity points and entropy rays: the loss
+    total and the gradients are those of train_step plus both terms."""
+    sc = synth.make_scene(3)
+    batch = synth.make_train_batch(3, 4096, seed=6)
+    pts = synth.sparsity_points(sc, 1 << 14)
+    erays = synth.entropy_rays(sc, 1 << 10)
+    s1 = om.scene_from_synth(sc, device="cuda")
+    tr = om.Trainer(s1, total_steps=100, lam_occ=0.0, lr=(1e-30, 1e-30), lr_occ=(1e-30, 1e-30))
+    loss = tr.step(batch["rays"], batch["target"], batch["smooth_dirs"], sparsity_points=pts, entropy_rays=erays)
+    torch.cuda.synchronize()
+    s2 = om.scene_from_synth(sc, device="cuda")
+    res = om.train_step(s2, batch["rays"], batch["target"], batch["smooth_dirs"], lam=(1.0, 0.1, 0.0))
+    osc = oracle.OracleScene(sc)
+    sp = oracle.sparsity(osc, pts, lam=0.05, want_grad=False)["loss"]
+    en = oracle.entropy(osc, erays, lam=1e-3, want_grad=False)["loss"]
+    torch.cuda.synchronize()
+    want = float(res["loss"][0]) + sp + en
+    assert float(loss[0]) == pytest.approx(want, rel=1e-5)
+    om.sparsity_loss(s2, pts, lam=0.05, grads=res["grads"])
+    om.entropy_loss(s2, erays, lam=1e-3, grads=res["grads"])
+    torch.cuda.synchronize()
+    for k in ("grid", "p_xy", "p_xz", "p_yz", "occ", "mlp"):
+        a, b = tr.grads[k], res["grads"][k]
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-7 * float(b.abs().max()) + 1e-30), k
