@@ -10,6 +10,7 @@ Functions follow Oblique-MERF (arXiv 2404.09531):
   camera_rays                                                  pinhole rays (FP32 rule)
   brick_table                                                  Sec. 4.4 brick allocation
   sparsity / entropy (loss + analytic gradient)                Eqs. 13, 14 (Sec. 4.3)
+  occupancy_grid / extract_bricks / plane_crop_rows            Sec. 4.4, Sec. 5.3 extraction
 
 Parity status: every function is pinned in tests/test_oracle*.py by closed
 forms, invariants, library routines or brute force (see that file).  No
@@ -61,6 +62,7 @@ class _Scene(ctypes.Structure):
         ("t_thr", ctypes.c_float),
         ("bg", ctypes.c_float * 3),
         ("n_max", ctypes.c_int32),
+        ("pz", ctypes.c_float * 2),
     ]
 
 
@@ -91,6 +93,12 @@ def _load():
         lib.or_ray_weights.argtypes = [P, P, P, P]
         lib.or_sparsity.restype = ctypes.c_double
         lib.or_sparsity.argtypes = [P, P, ctypes.c_long, ctypes.c_double, ctypes.c_double, P, P, P, P]
+        lib.or_occupancy_grid.restype = ctypes.c_long
+        lib.or_occupancy_grid.argtypes = [P, P, ctypes.c_int, P, P]
+        lib.or_extract_bricks.restype = None
+        lib.or_extract_bricks.argtypes = [P, ctypes.c_int, P, P, P, P]
+        lib.or_plane_crop_rows.restype = ctypes.c_int
+        lib.or_plane_crop_rows.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, P]
         lib.or_entropy.restype = ctypes.c_double
         lib.or_entropy.argtypes = [P, P, ctypes.c_long, ctypes.c_double, ctypes.c_double, P, P, P, P, P]
         _lib = lib
@@ -129,6 +137,8 @@ class OracleScene:
         self.n_max = int(over.get("n_max", spec.n_max))
         self.bg = np.asarray(over.get("bg", (0.0, 0.0, 0.0)), np.float32)
         self.brick = int(spec.brick if self.table is not None else 0)
+        pz = scene.get("plane_z")
+        self.pz = np.zeros(2, np.float32) if pz is None else np.asarray(pz, np.float32)
 
     def desc(self) -> _Scene:
         s = _Scene()
@@ -148,6 +158,7 @@ class OracleScene:
         s.t_thr = float(self.t_thr)
         s.bg[:] = [float(v) for v in self.bg]
         s.n_max = self.n_max
+        s.pz[:] = [float(v) for v in self.pz]
         return s
 
 
@@ -289,4 +300,36 @@ def entropy(oscene: OracleScene, rays, lam=1e-3, grad_scale=1.0, want_grad=True)
                               _ptr(g.get("grid")), _ptr(g.get("p_xy")), _ptr(g.get("p_xz")), _ptr(g.get("p_yz")),
                               _ptr(g.get("occ")))
     return {"loss": float(loss), "grads": g}
+
+
+def occupancy_grid(aabb, occ, N):
+    """Sec. 5.3: voxel occupancy [Nx][Ny][Nz] (uint8) from the occupancy plane, and the count."""
+    aabb = np.asarray(aabb, np.float32)
+    occ = np.ascontiguousarray(occ, np.float32)
+    N = np.asarray(N, np.int32)
+    out = np.zeros(tuple(int(v) for v in N), np.uint8)
+    cnt = _load().or_occupancy_grid(_ptr(aabb), _ptr(occ), occ.shape[0], _ptr(N), _ptr(out))
+    return out, int(cnt)
+
+
+def extract_bricks(L, B, table, src, src_table=None) -> np.ndarray:
+    """Brick pool for ``table`` from a dense grid or (with src_table) an older pool."""
+    L = np.asarray(L, np.int32)
+    table = np.ascontiguousarray(table, np.int32)
+    src = np.ascontiguousarray(src, np.float32)
+    st = None if src_table is None else np.ascontiguousarray(src_table, np.int32)
+    nb = int(table.max()) + 1 if table.size else 0
+    pool = np.zeros((max(nb, 0), B, B, B, 8), np.float32)
+    _load().or_extract_bricks(_ptr(L), int(B), _ptr(table), _ptr(src), _ptr(st), _ptr(pool))
+    return pool
+
+
+def plane_crop_rows(aabb, Rz, occ):
+    """Rows (k0, k1) of the XZ/YZ planes any evaluated sample touches and their z-range; None if empty."""
+    aabb = np.asarray(aabb, np.float32)
+    occ = np.ascontiguousarray(occ, np.float32)
+    rows = np.zeros(2, np.int32)
+    zr = np.zeros(2, np.float32)
+    rc = _load().or_plane_crop_rows(_ptr(aabb), int(Rz), _ptr(occ), occ.shape[0], _ptr(rows), _ptr(zr))
+    return None if rc != 0 else ((int(rows[0]), int(rows[1])), (float(zr[0]), float(zr[1])))
 

@@ -23,6 +23,9 @@
  *                   "occupied" (Sec. 4.4)
  *   sparsity loss   mean opacity of given points in the occupied space (Eq. 13)
  *   entropy loss    -sum p log p along top-down rays, p = M alpha / sum M alpha (Eq. 14)
+ *   extraction      3D occupancy grid from the occupancy plane (Sec. 5.3),
+ *                   brick pool from a grid or an older pool, XZ/YZ plane rows
+ *                   cropped to the occupancy bounds (Sec. 4.4)
  *
  * Readings of the paper taken here (all also used by the CUDA path):
  *   - the sample lattice is t_k = k * step (k >= 0) from the ray origin; which
@@ -82,6 +85,7 @@ typedef struct {
     float t_thr;             /* early termination threshold on T; 0 = off */
     float bg[3];             /* background colour */
     int32_t n_max;           /* maximum evaluated samples per ray */
+    float pz[2];             /* z-range spanned by the XZ and YZ planes; pz[1] <= pz[0]: the box's */
 } or_scene;
 
 /* one evaluated sample, kept for the backward sweep */
@@ -164,8 +168,12 @@ static void make_stencil(const or_scene *s, const double p[3], or_stencil *st, i
             }
     int pi[3];
     double pw[3];
-    for (int d = 0; d < 3; d++)
+    for (int d = 0; d < 2; d++)
         axis_coord(p[d], a[2 * d], a[2 * d + 1], s->R[d], &pi[d], &pw[d]);
+    if (s->pz[1] > s->pz[0])
+        axis_coord(p[2], s->pz[0], s->pz[1], s->R[2], &pi[2], &pw[2]);
+    else
+        axis_coord(p[2], a[4], a[5], s->R[2], &pi[2], &pw[2]);
     /* plane q spans axes (ax0, ax1): XY (0,1), XZ (0,2), YZ (1,2) */
     static const int AX[3][2] = {{0, 1}, {0, 2}, {1, 2}};
     for (int q = 0; q < 3; q++) {
@@ -824,5 +832,113 @@ double or_entropy(const or_scene *s, const float *rays, long n, double lam, doub
     }
     free(smp);
     return n > 0 ? lam * total / (double)n : 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* extraction after training (Sec. 4.4, Sec. 5.3)                      */
+/* ------------------------------------------------------------------ */
+
+/*
+ * 3D occupancy grid of N[0] x N[1] x N[2] voxels over the box.  Voxel
+ * (i, j, k) covers [x0 + i hx, x0 + (i + 1) hx) and the like; it is occupied
+ * iff some point in it would be evaluated by the sample rule: an occupancy
+ * cell overlapping its xy footprint (cells a with a/M < (i+1)/Nx and
+ * (a+1)/M > i/Nx, integer arithmetic) has a non-empty interval with
+ * z_min < z_hi and z_max > z_lo, where z_lo = z0 + k hz and z_hi = z0 +
+ * (k + 1) hz, hz = (z1 - z0) / Nz, all in FP32 without fused operations.
+ * out: one byte per voxel [Nx][Ny][Nz].  Returns the number occupied.
+ */
+long or_occupancy_grid(const float *aabb, const float *occ, int M, const int32_t *N, uint8_t *out)
+{
+    float hz = (aabb[5] - aabb[4]) / (float)N[2];
+    long count = 0;
+    for (long i = 0; i < N[0]; i++) {
+        long alo = i * M / N[0], ahi = ((i + 1) * M + N[0] - 1) / N[0] - 1;
+        for (long j = 0; j < N[1]; j++) {
+            long blo = j * M / N[1], bhi = ((j + 1) * M + N[1] - 1) / N[1] - 1;
+            for (long k = 0; k < N[2]; k++) {
+                float zlo = aabb[4] + (float)k * hz;
+                float zhi = aabb[4] + (float)(k + 1) * hz;
+                int hit = 0;
+                for (long a = alo; a <= ahi && !hit; a++)
+                    for (long b = blo; b <= bhi && !hit; b++) {
+                        float zmin = occ[2 * (a * M + b)], zmax = occ[2 * (a * M + b) + 1];
+                        if (zmin < zmax && zmin < zhi && zmax > zlo) hit = 1;
+                    }
+                out[(i * N[1] + j) * N[2] + k] = (uint8_t)hit;
+                count += hit;
+            }
+        }
+    }
+    return count;
+}
+
+/*
+ * Brick pool [nb][B][B][B][8] of the bricks that `table` allocates, taken
+ * from a dense grid [Lx][Ly][Lz][8] (src_table NULL) or from an older brick
+ * pool with table src_table (same B).  Vertices beyond the grid, or in a
+ * brick the source does not hold, are 0.
+ */
+void or_extract_bricks(const int32_t *L, int B, const int32_t *table, const float *src, const int32_t *src_table,
+                       float *pool)
+{
+    int nb[3];
+    for (int a = 0; a < 3; a++) nb[a] = (L[a] + B - 1) / B;
+    for (long bi = 0; bi < nb[0]; bi++)
+        for (long bj = 0; bj < nb[1]; bj++)
+            for (long bk = 0; bk < nb[2]; bk++) {
+                long t = (bi * nb[1] + bj) * nb[2] + bk;
+                long b = table[t];
+                if (b < 0) continue;
+                for (long li = 0; li < B; li++)
+                    for (long lj = 0; lj < B; lj++)
+                        for (long lk = 0; lk < B; lk++) {
+                            float *dst = pool + ((((b * B + li) * B + lj) * B) + lk) * NCH;
+                            long i = bi * B + li, j = bj * B + lj, k = bk * B + lk;
+                            const float *from = NULL;
+                            if (i < L[0] && j < L[1] && k < L[2]) {
+                                if (!src_table) {
+                                    from = src + ((i * L[1] + j) * L[2] + k) * NCH;
+                                } else if (src_table[t] >= 0) {
+                                    from = src + ((((long)src_table[t] * B + li) * B + lj) * B + lk) * NCH;
+                                }
+                            }
+                            for (int c = 0; c < NCH; c++) dst[c] = from ? from[c] : 0.0f;
+                        }
+            }
+}
+
+/*
+ * Rows [k0, k1] of the XZ and YZ planes (Rz rows over the box's z-range)
+ * that any evaluated sample can touch: samples lie strictly inside
+ * (lo, hi), the occupancy hull (min z_min, max z_max over non-empty cells),
+ * and the bilinear stencil reads rows floor(u) and floor(u) + 1 with u =
+ * (z - z0) * ((Rz - 1) / (z1 - z0)) in FP32; one row of margin on each side.
+ * zr = the cropped planes' z-range, z0 + k (z1 - z0) / (Rz - 1) in FP32.
+ * Returns 0, or -1 when no cell is occupied.
+ */
+int or_plane_crop_rows(const float *aabb, int Rz, const float *occ, int M, int32_t rows[2], float zr[2])
+{
+    float lo = INFINITY, hi = -INFINITY;
+    for (long c = 0; c < (long)M * M; c++) {
+        float a = occ[2 * c], b = occ[2 * c + 1];
+        if (!(a < b)) continue;
+        if (a < lo) lo = a;
+        if (b > hi) hi = b;
+    }
+    if (!(lo < hi)) return -1;
+    float sc = (float)(Rz - 1) / (aabb[5] - aabb[4]);
+    float ulo = (lo - aabb[4]) * sc, uhi = (hi - aabb[4]) * sc;
+    long k0 = (long)floorf(ulo) - 1, k1 = (long)floorf(uhi) + 2;
+    if (k0 < 0) k0 = 0;
+    if (k1 > Rz - 1) k1 = Rz - 1;
+    if (k0 > Rz - 2) k0 = Rz - 2;
+    if (k1 < k0 + 1) k1 = k0 + 1;
+    rows[0] = (int32_t)k0;
+    rows[1] = (int32_t)k1;
+    float h = (aabb[5] - aabb[4]) / (float)(Rz - 1);
+    zr[0] = aabb[4] + (float)k0 * h;
+    zr[1] = aabb[4] + (float)k1 * h;
+    return 0;
 }
 
