@@ -86,6 +86,9 @@ typedef struct {
     const void *plane_yz;      /* device, aligned like grid */
     const float *occ;          /* device: [M][M][2], 8-byte aligned */
     const float *mlp;          /* device: 883 float32 weights (always float32) */
+    float plane_z[2];          /* z-range spanned by the Rz rows of the XZ and YZ planes (a crop to the
+                                  occupancy bounds, Sec. 4.4); plane_z[1] <= plane_z[0], e.g. zeros:
+                                  the box's z-range */
 } omerf_scene_desc;
 
 /* Pinhole camera.  c2w is the 3x4 row-major camera-to-world matrix [R | o];
@@ -244,6 +247,66 @@ omerf_status omerf_sparsity_loss(const omerf_scene *scene, const float *points, 
 omerf_status omerf_entropy_loss(const omerf_scene *scene, const float *rays, int64_t n, float lambda,
                                 const float *grad_scale, float *loss, float *g_grid, float *g_xy,
                                 float *g_xz, float *g_yz, float *g_occ, void *stream);
+
+/* ---- extraction after training (Sec. 4.4, Sec. 5.3) ------------------ */
+
+/* 3D occupancy grid of N[0] x N[1] x N[2] voxels over the box, derived from
+ * the occupancy plane alone (the paper extracts one after training and
+ * reports its occupancy ratio, Sec. 5.3).  Voxel (i, j, k) covers
+ * [x0 + i hx, x0 + (i+1) hx) x [y0 + j hy, ...) x [z0 + k hz, z0 + (k+1) hz)
+ * and is occupied iff an occupancy cell a, b overlapping its xy footprint
+ * (a / M < (i + 1) / Nx and (a + 1) / M > i / Nx, same for b; exact integer
+ * arithmetic) has z_min < z_max, z_min < z_hi and z_max > z_lo, with z_lo =
+ * z0 + k hz, z_hi = z0 + (k + 1) hz and hz = (z1 - z0) / Nz in float32
+ * without fused operations: exactly the voxels holding a point the sample
+ * rule could evaluate.
+ *   aabb   host [6]; only z0, z1 and the occupancy cell layout matter
+ *   occ    device [M][M][2]
+ *   bits   device uint32 [Nx][Ny][ceil(Nz / 32)] (output): bit t of word w is
+ *          voxel k = 32 w + t; unused high bits of the last word are 0
+ *   count  device uint64 or NULL: the number of occupied voxels is ADDED
+ * One kernel launch. */
+omerf_status omerf_occupancy_grid(const float aabb[6], const float *occ, int32_t M, const int32_t N[3],
+                                  uint32_t *bits, unsigned long long *count, void *stream);
+
+/* Brick pool for a brick table (Sec. 4.4: the grid is stored as sparse
+ * bricks where the occupancy plane marks space as occupied; build the table
+ * with omerf_build_brick_table).  Brick b = table[bi][bj][bk] >= 0 receives
+ * vertices (bi B + li, bj B + lj, bk B + lk) of the source, which is a dense
+ * grid [Lx][Ly][Lz][8] (src_table NULL) or an older brick pool with table
+ * src_table (same grid_res and B; re-extraction after the occupancy plane
+ * changed).  Vertices beyond the grid, or in a brick the source does not
+ * hold, are 0.  Table entries >= n_bricks (and source entries >=
+ * src_n_bricks) are skipped.
+ *   table, src_table  device int32 [nbx][nby][nbz]
+ *   src, pool         device, feat_dtype elements, 16-byte aligned; pool holds
+ *                     n_bricks x B^3 x 8 values (output; must not overlap src)
+ * One kernel launch. */
+omerf_status omerf_extract_bricks(const int32_t grid_res[3], int32_t brick, const int32_t *table, int32_t n_bricks,
+                                  const void *src, const int32_t *src_table, int32_t src_n_bricks,
+                                  int32_t feat_dtype, void *pool, void *stream);
+
+/* Rows [k0, k1] of the XZ and YZ planes that any evaluated sample can read
+ * (Sec. 4.4: the planes' z-resolution follows the occupancy plane's bounds).
+ * Samples lie strictly inside (lo, hi), the hull of the non-empty cells;
+ * the stencil reads rows floor(u) and floor(u) + 1 with u = (z - plane_z[0])
+ * (Rz - 1) / (plane_z[1] - plane_z[0]) in float32; one row of margin on each
+ * side, clamped to [0, Rz - 1], at least two rows.
+ *   plane_z  host [2]: the z-range the current Rz rows span (the box's
+ *            z-range for uncropped planes)
+ *   rows     device int32 [2] (output): k0, k1, or -1, -1 if no cell is occupied
+ *   z_range  device float [2] (output): plane_z[0] + k (plane_z[1] -
+ *            plane_z[0]) / (Rz - 1) for k0 and k1, the cropped planes' plane_z
+ * One single-block kernel launch; the caller reads rows back to size the
+ * cropped planes. */
+omerf_status omerf_plane_crop_rows(const float plane_z[2], int32_t Rz, const float *occ, int32_t M,
+                                   int32_t *rows, float *z_range, void *stream);
+
+/* Copy rows [k0, k1] of a plane [n_outer][Rz][8] into [n_outer][k1-k0+1][8]
+ * (XZ: n_outer = Rx; YZ: n_outer = Ry).  src and dst device, feat_dtype
+ * elements, 16-byte aligned, not overlapping.  One kernel launch. */
+omerf_status omerf_crop_planes(const void *src, int64_t n_outer, int32_t Rz, int32_t k0, int32_t k1,
+                               int32_t feat_dtype, void *dst, void *stream);
 
 /* One parameter group of an Adam step: float32 master values, gradient and
  * moments (device, n values each, updated in place; moments start at zero),

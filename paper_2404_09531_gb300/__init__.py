@@ -13,10 +13,14 @@ from .binding import (  # noqa: F401
     adam_step,
     build_brick_table,
     camera_struct,
+    crop_planes,
     entropy_loss,
+    extract_bricks,
     lambda_occ,
     lib,
     lr_exponential,
+    occupancy_grid,
+    plane_crop_rows,
     ray_interval,
     render,
     render_noalloc,
@@ -27,10 +31,12 @@ from .binding import (  # noqa: F401
     train_bwd,
     train_fwd,
     train_step,
+    unpack_occupancy_bits,
 )
 
 __all__ = [
     "OmerfError", "Scene", "TrainStep", "Trainer", "adam_step", "build_brick_table", "camera_struct",
-    "entropy_loss", "lambda_occ", "lib", "lr_exponential", "ray_interval", "render", "render_noalloc",
-    "saved_bytes_per_ray", "scene_from_synth", "sparsity_loss", "sync", "train_bwd", "train_fwd", "train_step",
+    "crop_planes", "entropy_loss", "extract_bricks", "lambda_occ", "lib", "lr_exponential", "occupancy_grid",
+    "plane_crop_rows", "ray_interval", "render", "render_noalloc", "saved_bytes_per_ray", "scene_from_synth",
+    "sparsity_loss", "sync", "train_bwd", "train_fwd", "train_step", "unpack_occupancy_bits",
 ]

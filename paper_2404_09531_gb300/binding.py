@@ -41,6 +41,7 @@ class _SceneDesc(ctypes.Structure):
         ("plane_yz", ctypes.c_void_p),
         ("occ", ctypes.c_void_p),
         ("mlp", ctypes.c_void_p),
+        ("plane_z", ctypes.c_float * 2),
     ]
 
 
@@ -74,6 +75,10 @@ SIGNATURES = {
     "omerf_train_step": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "omerf_sparsity_loss": (ctypes.c_int, [_P, _P, _L, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P]),
     "omerf_entropy_loss": (ctypes.c_int, [_P, _P, _L, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "omerf_occupancy_grid": (ctypes.c_int, [_P, _P, _I, _P, _P, _P, _P]),
+    "omerf_extract_bricks": (ctypes.c_int, [_P, _I, _P, _I, _P, _P, _I, _I, _P, _P]),
+    "omerf_plane_crop_rows": (ctypes.c_int, [_P, _I, _P, _I, _P, _P, _P]),
+    "omerf_crop_planes": (ctypes.c_int, [_P, _L, _I, _I, _I, _I, _P, _P]),
     "omerf_adam_step": (ctypes.c_int, [_P, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, _L, _P]),
     "omerf_lr_exponential": (ctypes.c_float, [ctypes.c_float, ctypes.c_float, _L, _L]),
     "omerf_lambda_occ": (ctypes.c_float, [_L]),
@@ -147,13 +152,15 @@ class Scene:
       table    int32 brick table [nbx, nby, nbz] (brick grids) or None
       p_xy, p_xz, p_yz   planes [Rx, Ry, 8], [Rx, Rz, 8], [Ry, Rz, 8]
       occ      float32 [M, M, 2]      mlp float32 [883]
+      plane_z  (z0, z1) the z-range of the XZ/YZ planes' Rz rows when they are
+               cropped to the occupancy bounds (crop_planes); None = the box's
     Features are float32 or bfloat16 (both grid and planes the same dtype).
     The tensors are referenced, not copied: in-place updates are seen by the
     next call (call update() after changing occ).
     """
 
     def __init__(self, *, aabb, grid, p_xy, p_xz, p_yz, occ, mlp, step, eps, t_thr=1e-4, n_max=128,
-                 bg=(0.0, 0.0, 0.0), table=None, brick=0, grid_res=None, stream=None):
+                 bg=(0.0, 0.0, 0.0), table=None, brick=0, grid_res=None, plane_z=None, stream=None):
         self.grid, self.table = grid, table
         self.p_xy, self.p_xz, self.p_yz = p_xy, p_xz, p_yz
         self.occ, self.mlp = occ, mlp
@@ -178,6 +185,7 @@ class Scene:
         self.aabb = tuple(float(np.float32(v)) for v in aabb)
         self.step, self.eps, self.t_thr, self.n_max = float(step), float(eps), float(t_thr), int(n_max)
         self.bg = tuple(float(v) for v in bg)
+        self.plane_z = None if plane_z is None else tuple(float(np.float32(v)) for v in plane_z)
         d = _SceneDesc()
         d.aabb[:] = list(self.aabb)
         d.grid_res[:] = list(self.grid_res)
@@ -193,6 +201,7 @@ class Scene:
         d.brick_table = table.data_ptr() if table is not None else None
         d.plane_xy, d.plane_xz, d.plane_yz = p_xy.data_ptr(), p_xz.data_ptr(), p_yz.data_ptr()
         d.occ, d.mlp = occ.data_ptr(), mlp.data_ptr()
+        d.plane_z[:] = list(self.plane_z) if self.plane_z is not None else [0.0, 0.0]
         self._desc = d
         h = ctypes.c_void_p()
         _check(lib().omerf_scene_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)), "omerf_scene_create")
@@ -266,7 +275,8 @@ def scene_from_synth(sc: dict, device="cuda", feat_dtype=None, table=None, strea
               p_xz=torch.as_tensor(sc["p_xz"]).to(device=device, dtype=dt).contiguous(),
               p_yz=torch.as_tensor(sc["p_yz"]).to(device=device, dtype=dt).contiguous(),
               occ=occ, mlp=torch.as_tensor(sc["mlp"], dtype=torch.float32).to(device).contiguous(),
-              step=spec.step, eps=spec.eps, t_thr=spec.t_thr, n_max=spec.n_max, stream=stream)
+              step=spec.step, eps=spec.eps, t_thr=spec.t_thr, n_max=spec.n_max, stream=stream,
+              plane_z=sc.get("plane_z"))
     kw.update(over)
     return Scene(**kw)
 
@@ -451,6 +461,91 @@ def entropy_loss(scene, rays, lam=1e-3, grads=None, loss=None, grad_scale=None, 
                                     _ptr(loss), _ptr(g.get("grid")), _ptr(g.get("p_xy")), _ptr(g.get("p_xz")),
                                     _ptr(g.get("p_yz")), _ptr(g.get("occ")), _stream(stream)), "omerf_entropy_loss")
     return loss
+
+
+def _feat_enum(t):
+    if t.dtype == torch.float32:
+        return OMERF_F32
+    if t.dtype == torch.bfloat16:
+        return OMERF_BF16
+    raise OmerfError("features must be float32 or bfloat16")
+
+
+def occupancy_grid(aabb, occ, N, stream=None):
+    """Sec. 5.3 occupancy grid from the occupancy plane: (bits uint32 tensor
+    [Nx, Ny, ceil(Nz/32)] viewed as int32, count tensor [1] int64)."""
+    _require_cuda(occ, "occ")
+    N = [int(v) for v in N]
+    bits = torch.empty((N[0], N[1], (N[2] + 31) // 32), dtype=torch.int32, device=occ.device)
+    count = torch.zeros(1, dtype=torch.int64, device=occ.device)
+    a = (ctypes.c_float * 6)(*[float(v) for v in aabb])
+    n = (ctypes.c_int32 * 3)(*N)
+    _check(lib().omerf_occupancy_grid(a, _ptr(occ), int(occ.shape[0]), n, _ptr(bits), _ptr(count),
+                                      _stream(stream)), "omerf_occupancy_grid")
+    return bits, count
+
+
+def unpack_occupancy_bits(bits, Nz):
+    """[Nx, Ny, W] int32 words -> bool [Nx, Ny, Nz] (host numpy)."""
+    w = np.asarray(bits.cpu().numpy() if hasattr(bits, "cpu") else bits).view(np.uint32)
+    shifts = np.arange(32, dtype=np.uint32)
+    out = ((w[..., None] >> shifts) & 1).astype(bool).reshape(w.shape[0], w.shape[1], -1)
+    return out[..., :Nz]
+
+
+def extract_bricks(grid_res, brick, table, src, src_table=None, n_bricks=None, src_n_bricks=None, stream=None):
+    """Sec. 4.4 brick pool for ``table`` from a dense grid or an older pool
+    (``src_table``); returns the new pool tensor [n_bricks, B, B, B, 8]."""
+    _require_cuda(table, "table")
+    _require_cuda(src, "src")
+    if n_bricks is None:
+        n_bricks = int(table.max().item()) + 1 if table.numel() else 0
+    if src_table is not None:
+        _require_cuda(src_table, "src_table")
+        if src_n_bricks is None:
+            src_n_bricks = int(src.shape[0])
+    B = int(brick)
+    pool = torch.empty((max(int(n_bricks), 0), B, B, B, 8), dtype=src.dtype, device=src.device)
+    if n_bricks == 0:
+        return pool
+    g = (ctypes.c_int32 * 3)(*[int(v) for v in grid_res])
+    _check(lib().omerf_extract_bricks(g, B, _ptr(table), int(n_bricks), _ptr(src), _ptr(src_table),
+                                      int(src_n_bricks or 0), _feat_enum(src), _ptr(pool), _stream(stream)),
+           "omerf_extract_bricks")
+    return pool
+
+
+def plane_crop_rows(scene, stream=None):
+    """Rows (k0, k1) of the scene's XZ/YZ planes any evaluated sample reads and
+    the cropped z-range, or None if no cell is occupied (one small readback)."""
+    rows = torch.empty(2, dtype=torch.int32, device=scene.device)
+    zr = torch.empty(2, dtype=torch.float32, device=scene.device)
+    pz = scene.plane_z if scene.plane_z is not None else (scene.aabb[4], scene.aabb[5])
+    _check(lib().omerf_plane_crop_rows((ctypes.c_float * 2)(*pz), int(scene.plane_res[2]), _ptr(scene.occ),
+                                       int(scene.occ_res), _ptr(rows), _ptr(zr), _stream(stream)),
+           "omerf_plane_crop_rows")
+    r = rows.cpu().tolist()
+    if r[0] < 0:
+        return None
+    return (r[0], r[1]), tuple(float(v) for v in zr.cpu().tolist())
+
+
+def crop_planes(scene, stream=None):
+    """A new Scene whose XZ and YZ planes keep only the rows any evaluated
+    sample reads (Sec. 4.4); grid, XY plane, occupancy and MLP are shared."""
+    cr = plane_crop_rows(scene, stream)
+    if cr is None:
+        raise OmerfError("the occupancy plane is empty")
+    (k0, k1), zr = cr
+    out = []
+    for p in (scene.p_xz, scene.p_yz):
+        dst = torch.empty((p.shape[0], k1 - k0 + 1, 8), dtype=p.dtype, device=p.device)
+        _check(lib().omerf_crop_planes(_ptr(p), int(p.shape[0]), int(p.shape[1]), k0, k1, _feat_enum(p), _ptr(dst),
+                                       _stream(stream)), "omerf_crop_planes")
+        out.append(dst)
+    return Scene(aabb=scene.aabb, grid=scene.grid, table=scene.table, brick=scene.brick, grid_res=scene.grid_res,
+                 p_xy=scene.p_xy, p_xz=out[0], p_yz=out[1], occ=scene.occ, mlp=scene.mlp, step=scene.step,
+                 eps=scene.eps, t_thr=scene.t_thr, n_max=scene.n_max, bg=scene.bg, plane_z=zr, stream=stream)
 
 
 class _AdamGroup(ctypes.Structure):

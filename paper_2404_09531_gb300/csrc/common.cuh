@@ -26,7 +26,8 @@ constexpr int kSavedFloats = 20;
 struct Geo {
   float lo[3], hi[3];      // box
   float gs[3];             // grid: (L - 1) / (hi - lo)
-  float ps[3];             // planes: (R - 1) / (hi - lo)
+  float ps[3];             // planes: (R - 1) / (plane extent)
+  float plo[3];            // planes: lower end of each axis (z may be cropped to the occupancy bounds)
   int L[3], R[3];
   float osx, osy;          // occupancy cells: M / (hi - lo), float32 as in the decision rule
   int M;
@@ -292,7 +293,7 @@ __device__ __forceinline__ void plane_stencil(const Geo& g, const float p[3], in
   int i[3];
   float f[3];
 #pragma unroll
-  for (int a = 0; a < 3; a++) axis_coord(p[a], g.lo[a], g.ps[a], g.R[a], i[a], f[a]);
+  for (int a = 0; a < 3; a++) axis_coord(p[a], g.plo[a], g.ps[a], g.R[a], i[a], f[a]);
   const int U[3] = {0, 0, 1}, V[3] = {1, 2, 2};
 #pragma unroll
   for (int q = 0; q < 3; q++) {

@@ -268,6 +268,7 @@ omerf_status validate_desc(const omerf_scene_desc* d) {
   if (d->n_max < 1 || d->n_max > 65536) { set_error("n_max must be in 1..65536"); return OMERF_EINVAL; }
   for (int j = 0; j < 3; j++)
     if (!std::isfinite(d->bg[j])) { set_error("bg must be finite"); return OMERF_EINVAL; }
+  if (!std::isfinite(d->plane_z[0]) || !std::isfinite(d->plane_z[1])) { set_error("plane_z must be finite"); return OMERF_EINVAL; }
   if (d->brick != 0) {
     if (d->brick < 2 || d->brick > 32 || (d->brick & (d->brick - 1))) { set_error("brick must be 0 or a power of two in 2..32"); return OMERF_EINVAL; }
     if (!d->brick_table) { set_error("brick_table is NULL for a brick grid"); return OMERF_EINVAL; }
@@ -312,7 +313,12 @@ void fill_geo(omerf_scene* s) {
     g.L[a] = d.grid_res[a];
     g.R[a] = d.plane_res[a];
     g.gs[a] = (float)(d.grid_res[a] - 1) / (g.hi[a] - g.lo[a]);
+    g.plo[a] = g.lo[a];
     g.ps[a] = (float)(d.plane_res[a] - 1) / (g.hi[a] - g.lo[a]);
+  }
+  if (d.plane_z[1] > d.plane_z[0]) {
+    g.plo[2] = d.plane_z[0];
+    g.ps[2] = (float)(d.plane_res[2] - 1) / (d.plane_z[1] - d.plane_z[0]);
   }
   // the decision rule's cell scale: float32 M / (x1 - x0)
   g.osx = (float)d.occ_res / (g.hi[0] - g.lo[0]);

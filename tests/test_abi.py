@@ -80,6 +80,17 @@ def test_host_validation_without_gpu(lib):
     assert lib.omerf_sparsity_loss(None, None, 0, 0.05, None, None, None, None, None, None, None) == -1
     assert lib.omerf_entropy_loss(None, None, 0, 1e-3, None, None, None, None, None, None, None, None) == -1
     assert b"NULL scene" in lib.omerf_last_error()
+    # extraction entry points validate sizes before launching
+    aabb = (ctypes.c_float * 6)(-1, 1, -1, 1, -1, 1)
+    n = (ctypes.c_int32 * 3)(4, 4, 0)
+    assert lib.omerf_occupancy_grid(aabb, ctypes.c_void_p(4096), 2, n, ctypes.c_void_p(4096), None, None) == -2
+    g = (ctypes.c_int32 * 3)(8, 8, 8)
+    assert lib.omerf_extract_bricks(g, 3, ctypes.c_void_p(4096), 1, ctypes.c_void_p(4096), None, 0, 0,
+                                    ctypes.c_void_p(4096), None) == -1
+    pz = (ctypes.c_float * 2)(0.5, 0.5)
+    assert lib.omerf_plane_crop_rows(pz, 8, ctypes.c_void_p(4096), 2, ctypes.c_void_p(4096),
+                                     ctypes.c_void_p(4096), None) == -1
+    assert lib.omerf_crop_planes(ctypes.c_void_p(4096), 4, 8, 5, 5, 0, ctypes.c_void_p(8192), None) == -2
 
 
 def test_host_schedules_match_reference(lib):
