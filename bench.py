@@ -293,6 +293,42 @@ def bench_precision_train(om, torch, dev, steps, warmup, flush, stream, n_rays=1
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
+def bench_extraction(om, torch, scene, steps, warmup, flush, stream, N=(2048, 2048, 128)):
+    """Extraction after training (Sec. 4.4, Sec. 5.3) on the city scene, each
+    stage timed with events: the 3D occupancy grid at the paper's largest
+    resolution, the brick table and a pool re-extraction from the current
+    pool, and the XZ/YZ plane crop (rows + copy)."""
+    st = {"grid": [], "bricks": [], "crop": []}
+    bits = count = None
+    for it in range(warmup + steps):
+        flush.fill_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        bits, count = om.occupancy_grid(scene.aabb, scene.occ, N)
+        ev[1].record(stream)
+        table, n_alloc = om.build_brick_table(scene.aabb, scene.grid_res, scene.brick, scene.occ)
+        pool = om.extract_bricks(scene.grid_res, scene.brick, table, scene.grid, src_table=scene.table,
+                                 n_bricks=int(scene.grid.shape[0]))
+        ev[2].record(stream)
+        cropped = om.crop_planes(scene)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        if it >= warmup:
+            st["grid"].append(ev[0].elapsed_time(ev[1]))
+            st["bricks"].append(ev[1].elapsed_time(ev[2]))
+            st["crop"].append(ev[2].elapsed_time(ev[3]))
+        del pool, cropped
+    voxels = N[0] * N[1] * N[2]
+    ms = {k: float(np.mean(v)) for k, v in st.items()}
+    return {"occupancy_grid": {"ms": ms["grid"], "voxels": voxels, "resolution": list(N),
+                               "occupancy_ratio": int(count.item()) / voxels},
+            "bricks": {"ms": ms["bricks"], "n_bricks": int(scene.grid.shape[0]),
+                       "note": "table from the occupancy plane + pool re-extraction from the current pool"},
+            "plane_crop": {"ms": ms["crop"], "note": "crop rows (one 8-byte readback) + XZ/YZ row copy"},
+            "total_ms": sum(ms.values()),
+            "paper": "extracting the occupancy grid takes 2 to 10 minutes in the paper (Sec. 5.3)"}
+
+
 def run_native(args):
     import torch
 
@@ -445,6 +481,8 @@ def run_native(args):
         adam_ms.append(c.elapsed_time(e))
     t_loop, t_adam = float(np.mean(loop_ms)), float(np.mean(adam_ms))
 
+    extraction = bench_extraction(om, torch, scene, max(1, min(args.steps, 5)), args.warmup, flush, stream)
+
     precision = None
     if not args.no_precision:
         psteps = max(1, min(args.steps, 5))
@@ -488,6 +526,7 @@ def run_native(args):
                   "adam": {"us": t_adam * 1e3, "params": n_params,
                            "achieved_gbs": 28.0 * n_params / (t_adam * 1e-3) / 1e9,
                            "note": "28 B per parameter (read p, g, m, v; write p, m, v)"}},
+        "extraction": extraction,
         "gpu_launches": args.steps * len(cams),
         "clocks": clk,
     }
