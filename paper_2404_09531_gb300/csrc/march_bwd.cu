@@ -5,8 +5,9 @@
 //  1. each lane recomputes its ray's deferred MLP G(F, d) (Eq. 4) and the
 //     smoothness evaluations G(F, s_k) (Eqs. 9-10), forms dL/dC of the
 //     Charbonnier loss (Eq. 12) and backpropagates to dL/dF, dL/dT_N and the
-//     MLP weights.  Weight gradients are staged per warp in shared memory and
-//     summed over the 32 rays by lanes that own disjoint weights;
+//     layer deltas.  The 32 rays' activations and deltas are staged in shared
+//     memory and the weight gradient, a sum over rays, is accumulated on
+//     tensor cores (mma.sync TF32, split operands) in registers;
 //  2. the warp re-marches every ray of the bundle exactly like the forward
 //     (same lattice windows, same product scan) for its saved sample count,
 //     and converts dL/dF into per-sample gradients:
@@ -33,7 +34,6 @@ constexpr int kBwdThreads = 128;   // 4 warps per CTA
 #define OMERF_RUN_PLANE 1  // and plane-texel runs over up to 2^1 lanes
 #endif
 constexpr int kRow = 101;          // staged floats per ray: x 34, h1 16, h2 16, g1 16, g2 16, g3 3
-constexpr int kOwned = (kMlpParams + 31) / 32;  // weights owned per lane (28)
 
 struct BwdArgs {
   const float* rays;
@@ -162,32 +162,137 @@ __device__ __forceinline__ void zero_row(float* __restrict__ row) {
   for (int i = 0; i < kRow; i++) row[i] = 0.0f;
 }
 
-// Sum the staged weight gradient of the warp's 32 rows into the warp's
-// accumulator; lane l owns weights l, l + 32, ...
-__device__ __forceinline__ void accumulate_rows(const float* __restrict__ rows, int lane, float* __restrict__ dW) {
+// ---------------------------------------------------------------------------
+// Weight-gradient accumulation on tensor cores.  The MLP weight gradient of a
+// warp's 32 staged rows is three small GEMMs whose reduction dimension is the
+// rays:  [dW1 | db1] (16 x 35) += G1^T [16 x 32] . [X | 1] [32 x 35],
+//        [dW2 | db2] (16 x 17) += G2^T . [H1 | 1],
+//        [dW3 | db3]^T (17 x 3) += [H2 | 1]^T . G3.
+// They run as mma.sync m16n8k8 TF32 with each operand split into a TF32 part
+// and a TF32 residual (three products, hi.hi + hi.lo + lo.hi), about FP32
+// accurate; the FP32 accumulators stay in registers for the whole persistent
+// loop, in the m16n8 accumulator layout (c0: row g, col 2t; c1: row g, col
+// 2t+1; c2, c3: row g + 8), g = lane / 4, t = lane % 4.
+struct DwAcc {
+  float w1[5][4];  // units x (34 inputs, bias, pad): 5 column tiles of 8
+  float w2[3][4];  // units x (16 inputs, bias, pad)
+  float w3[2][4];  // (16 inputs, bias, pad) x (3 outputs, pad): 2 row tiles
+};
+
+__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(v));
+  const float r = v - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
+__device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// c += A . B with A = (ah + al), B = (b0, b1) split here: three TF32 products.
+__device__ __forceinline__ void mma3(float c[4], const uint32_t ah[4], const uint32_t al[4], float b0, float b1) {
+  uint32_t bh0, bl0, bh1, bl1;
+  split_tf32(b0, bh0, bl0);
+  split_tf32(b1, bh1, bl1);
+  mma_tf32(c, al, bh0, bh1);
+  mma_tf32(c, ah, bl0, bl1);
+  mma_tf32(c, ah, bh0, bh1);
+}
+
+__device__ __forceinline__ void zero_acc(DwAcc& acc) {
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+#pragma unroll
+    for (int j = 0; j < 5; j++) acc.w1[j][i] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; j++) acc.w2[j][i] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 2; j++) acc.w3[j][i] = 0.0f;
+  }
+}
+
+// Add the warp's 32 staged rows (x 0..33, h1 34..49, h2 50..65, g1 66..81,
+// g2 82..97, g3 98..100) to the accumulators.  All 32 lanes must call it.
+__device__ __forceinline__ void accumulate_mma(const float* __restrict__ rows, int lane, DwAcc& acc) {
   __syncwarp();
+  const int g = lane >> 2, t = lane & 3;
 #pragma unroll 1
-  for (int m = 0; m < kOwned; m++) {
-    const int w = lane + 32 * m;
-    if (w >= kMlpParams) break;
-    int da, aa;  // delta column, activation column (-1: bias)
-    if (w < kOffB1) { da = 66 + w / 34; aa = w % 34; }
-    else if (w < kOffW2) { da = 66 + (w - kOffB1); aa = -1; }
-    else if (w < kOffB2) { da = 82 + ((w - kOffW2) >> 4); aa = 34 + ((w - kOffW2) & 15); }
-    else if (w < kOffW3) { da = 82 + (w - kOffB2); aa = -1; }
-    else if (w < kOffB3) { da = 98 + ((w - kOffW3) >> 4); aa = 50 + ((w - kOffW3) & 15); }
-    else { da = 98 + (w - kOffB3); aa = -1; }
-    float s = 0.0f;
-    if (aa >= 0) {
-#pragma unroll 8
-      for (int r = 0; r < 32; r++) s = fmaf(rows[r * kRow + da], rows[r * kRow + aa], s);
-    } else {
-#pragma unroll 8
-      for (int r = 0; r < 32; r++) s += rows[r * kRow + da];
+  for (int s = 0; s < 4; s++) {  // rays 8 s .. 8 s + 7 (the k dimension)
+    const float* r0 = rows + (8 * s + t) * kRow;
+    const float* r1 = rows + (8 * s + t + 4) * kRow;
+    uint32_t ah[4], al[4];
+    // layer 1: A = G1^T (unit x ray), B = [X | 1] (ray x input)
+    split_tf32(r0[66 + g], ah[0], al[0]);
+    split_tf32(r0[74 + g], ah[1], al[1]);
+    split_tf32(r1[66 + g], ah[2], al[2]);
+    split_tf32(r1[74 + g], ah[3], al[3]);
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+      const int c = 8 * j + g;
+      const float b0 = c < 34 ? r0[c] : (c == 34 ? 1.0f : 0.0f);
+      const float b1 = c < 34 ? r1[c] : (c == 34 ? 1.0f : 0.0f);
+      mma3(acc.w1[j], ah, al, b0, b1);
     }
-    dW[w] += s;
+    // layer 2: A = G2^T, B = [H1 | 1]
+    split_tf32(r0[82 + g], ah[0], al[0]);
+    split_tf32(r0[90 + g], ah[1], al[1]);
+    split_tf32(r1[82 + g], ah[2], al[2]);
+    split_tf32(r1[90 + g], ah[3], al[3]);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      const int c = 8 * j + g;
+      const float b0 = c < 16 ? r0[34 + c] : (c == 16 ? 1.0f : 0.0f);
+      const float b1 = c < 16 ? r1[34 + c] : (c == 16 ? 1.0f : 0.0f);
+      mma3(acc.w2[j], ah, al, b0, b1);
+    }
+    // layer 3 (transposed): A = [H2 | 1]^T (input x ray), B = G3 (ray x output)
+    const float b0 = g < 3 ? r0[98 + g] : 0.0f;
+    const float b1 = g < 3 ? r1[98 + g] : 0.0f;
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++) {
+      const int i0 = 16 * mt + g, i1 = i0 + 8;
+      split_tf32(i0 < 16 ? r0[50 + i0] : (i0 == 16 ? 1.0f : 0.0f), ah[0], al[0]);
+      split_tf32(i1 < 16 ? r0[50 + i1] : (i1 == 16 ? 1.0f : 0.0f), ah[1], al[1]);
+      split_tf32(i0 < 16 ? r1[50 + i0] : (i0 == 16 ? 1.0f : 0.0f), ah[2], al[2]);
+      split_tf32(i1 < 16 ? r1[50 + i1] : (i1 == 16 ? 1.0f : 0.0f), ah[3], al[3]);
+      mma3(acc.w3[mt], ah, al, b0, b1);
+    }
   }
   __syncwarp();
+}
+
+// Store the accumulators as weight-gradient sums indexed like the 883
+// parameters (every parameter is held by exactly one lane and element).
+__device__ __forceinline__ void store_acc(const DwAcc& acc, int lane, float* __restrict__ dW) {
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    const int r = g + 8 * (e >> 1), cc = 2 * t + (e & 1);
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+      const int c = 8 * j + cc;  // unit r, input c
+      if (c < 34) dW[kOffW1 + r * 34 + c] = acc.w1[j][e];
+      else if (c == 34) dW[kOffB1 + r] = acc.w1[j][e];
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      const int c = 8 * j + cc;
+      if (c < 16) dW[kOffW2 + r * 16 + c] = acc.w2[j][e];
+      else if (c == 16) dW[kOffB2 + r] = acc.w2[j][e];
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++) {
+      const int i = 16 * mt + r;  // input i, output cc
+      if (cc < 3) {
+        if (i < 16) dW[kOffW3 + cc * 16 + i] = acc.w3[mt][e];
+        else if (i == 16) dW[kOffB3 + cc] = acc.w3[mt][e];
+      }
+    }
+  }
 }
 
 // Scatter w * dt to the texel at element offset `off`, first summing runs of
@@ -439,15 +544,16 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* sW = smem;                                   // padded MLP weights
   float* sWT = smem + kSmemMlp;                       // transposed weights for the backward
-  float* sDWall = smem + kSmemMlp + kSmemT;           // 884 per warp: weight-gradient sums
-  float* sDW = sDWall + warp * 884;
-  float* rows = sDWall + 884 * (kBwdThreads / 32) + warp * 32 * kRow;
+  float* rowsAll = smem + kSmemMlp + kSmemT;          // 32 staged rows per warp
+  float* rows = rowsAll + warp * 32 * kRow;
   load_mlp_padded(g.mlp, sW);
   load_mlp_transposed(g.mlp, sWT);
-  for (int i = threadIdx.x; i < 884 * (kBwdThreads / 32); i += blockDim.x) sDWall[i] = 0.0f;
   __syncthreads();
   const float gs = a.grad_scale ? __ldg(a.grad_scale) : 1.0f;
   const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+  const bool want_dw = a.g_mlp != nullptr;
+  DwAcc acc;
+  zero_acc(acc);
   for (long b = (long)blockIdx.x * (blockDim.x >> 5) + warp; b < a.n_bundles; b += nwarps) {
     const long rid = b * 32 + lane;
     const bool valid = rid < a.n;
@@ -502,7 +608,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
       } else {
         zero_row(row);
       }
-      accumulate_rows(rows, lane, sDW);
+      if (want_dw) accumulate_mma(rows, lane, acc);
     }
     if (live) {
       float y[3];
@@ -511,7 +617,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
     } else {
       zero_row(row);
     }
-    accumulate_rows(rows, lane, sDW);
+    if (want_dw) accumulate_mma(rows, lane, acc);
     if (valid) {
 #pragma unroll
       for (int j = 0; j < 3; j++) gF[j] += gC[j];
@@ -521,14 +627,16 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
       sv[4] = make_float4(gF[4], gF[5], gF[6], gT);
     }
   }
-  // weight gradients: per-warp sums -> CTA sum -> one global add per CTA
+  // weight gradients: per-warp sums (in the staging area, no longer needed)
+  // -> CTA sum -> one global add per CTA
+  if (!want_dw) return;
   __syncthreads();
-  if (a.g_mlp) {
-    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
-      float v = 0.0f;
-      for (int w = 0; w < kBwdThreads / 32; w++) v += sDWall[w * 884 + i];
-      atomicAdd(a.g_mlp + i, v);
-    }
+  store_acc(acc, lane, rowsAll + warp * kMlpParams);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
+    float v = 0.0f;
+    for (int w = 0; w < kBwdThreads / 32; w++) v += rowsAll[w * kMlpParams + i];
+    atomicAdd(a.g_mlp + i, v);
   }
 }
 
@@ -594,7 +702,7 @@ static cudaError_t launch_bwd_variant(const omerf_scene* s, const BwdArgs& a, cu
 }
 
 static cudaError_t launch_mlp_bwd(const omerf_scene* s, const BwdArgs& a, cudaStream_t stream) {
-  const size_t smem = (size_t)(kSmemMlp + kSmemT + 884 * (kBwdThreads / 32) + (kBwdThreads / 32) * 32 * kRow) * sizeof(float);
+  const size_t smem = (size_t)(kSmemMlp + kSmemT + (kBwdThreads / 32) * 32 * kRow) * sizeof(float);
   static int blocks[64] = {0};
   const int dev = s->device & 63;
   if (blocks[dev] == 0) {
