@@ -27,7 +27,6 @@ struct Geo {
   float lo[3], hi[3];      // box
   float gs[3];             // grid: (L - 1) / (hi - lo)
   float ps[3];             // planes: (R - 1) / (plane extent)
-  float plo[3];            // planes: lower end of each axis (z may be cropped to the occupancy bounds)
   int L[3], R[3];
   float osx, osy;          // occupancy cells: M / (hi - lo), float32 as in the decision rule
   int M;
@@ -48,6 +47,9 @@ struct Geo {
   const float2* chull;     // device [Mc][Mc]: coarse max-pooled (min z_min, max z_max)
   int clog2;               // coarse cell = 2^clog2 x 2^clog2 occupancy cells
   int Mc;                  // coarse cells per axis
+  // planes: texel offset of a z-range cropped to the occupancy bounds,
+  // (z0' - z0) ps[2] (last, so that the fields above keep their offsets)
+  float pzoff;
 };
 
 struct Cam {
@@ -203,8 +205,8 @@ __device__ __forceinline__ float occupancy(const Geo& g, float z, float2 zb, int
 // feature gather (Eq. 2): 8 grid corners + 3 x 4 plane texels, 8 channels each
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void axis_coord(float x, float lo, float s, int L, int& i, float& w) {
-  float u = (x - lo) * s;
+__device__ __forceinline__ void axis_coord(float x, float lo, float s, int L, int& i, float& w, float off = 0.0f) {
+  float u = fmaf(x - lo, s, -off);
   u = fminf(fmaxf(u, 0.0f), (float)(L - 1));
   i = min((int)u, L - 2);
   w = u - (float)i;
@@ -293,7 +295,8 @@ __device__ __forceinline__ void plane_stencil(const Geo& g, const float p[3], in
   int i[3];
   float f[3];
 #pragma unroll
-  for (int a = 0; a < 3; a++) axis_coord(p[a], g.plo[a], g.ps[a], g.R[a], i[a], f[a]);
+  // (x - x0) is shared with the grid stencil; z counts from a cropped range
+  for (int a = 0; a < 3; a++) axis_coord(p[a], g.lo[a], g.ps[a], g.R[a], i[a], f[a], a == 2 ? g.pzoff : 0.0f);
   const int U[3] = {0, 0, 1}, V[3] = {1, 2, 2};
 #pragma unroll
   for (int q = 0; q < 3; q++) {

@@ -313,12 +313,12 @@ void fill_geo(omerf_scene* s) {
     g.L[a] = d.grid_res[a];
     g.R[a] = d.plane_res[a];
     g.gs[a] = (float)(d.grid_res[a] - 1) / (g.hi[a] - g.lo[a]);
-    g.plo[a] = g.lo[a];
     g.ps[a] = (float)(d.plane_res[a] - 1) / (g.hi[a] - g.lo[a]);
   }
+  g.pzoff = 0.0f;
   if (d.plane_z[1] > d.plane_z[0]) {
-    g.plo[2] = d.plane_z[0];
     g.ps[2] = (float)(d.plane_res[2] - 1) / (d.plane_z[1] - d.plane_z[0]);
+    g.pzoff = (d.plane_z[0] - g.lo[2]) * g.ps[2];
   }
   // the decision rule's cell scale: float32 M / (x1 - x0)
   g.osx = (float)d.occ_res / (g.hi[0] - g.lo[0]);
