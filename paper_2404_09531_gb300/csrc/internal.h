@@ -36,7 +36,7 @@ cudaError_t launch_march_fwd(const omerf_scene* s, const Cam* cam, const float* 
 cudaError_t launch_march_bwd(const omerf_scene* s, const float* rays, const float* target, const float* dirs,
                              long n, int K, const float lam[3], float* saved, const float* grad_scale,
                              float* g_grid, float* g_xy, float* g_xz, float* g_yz, float* g_occ,
-                             float* g_mlp, cudaStream_t stream);
+                             float* g_mlp, float* loss, cudaStream_t stream);
 
 int persistent_blocks(const void* kernel, int threads, size_t smem, int num_sms);
 

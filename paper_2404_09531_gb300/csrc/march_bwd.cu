@@ -50,6 +50,7 @@ struct BwdArgs {
   float* g_yz;
   float* g_occ;
   float* g_mlp;
+  float* loss;  // device [4] or NULL: the Charbonnier and smoothness terms are added (fused step)
   unsigned* counter;
 };
 
@@ -554,6 +555,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
   const bool want_dw = a.g_mlp != nullptr;
   DwAcc acc;
   zero_acc(acc);
+  float l_rgb = 0.0f, l_smooth = 0.0f;
   for (long b = (long)blockIdx.x * (blockDim.x >> 5) + warp; b < a.n_bundles; b += nwarps) {
     const long rid = b * 32 + lane;
     const bool valid = rid < a.n;
@@ -581,12 +583,23 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
         e[j] = F[j] + yd[j] + TN * g.bg[j] - __ldg(a.target + 3 * rid + j);
         e2 = fmaf(e[j], e[j], e2);
       }
-      const float inv_ell = 1.0f / sqrtf(e2 + 1e-6f);
+      const float ell = sqrtf(e2 + 1e-6f);
+      const float inv_ell = 1.0f / ell;
+      l_rgb += ell;
 #pragma unroll
       for (int j = 0; j < 3; j++) {
         gC[j] = gs * a.lam_rgb * e[j] * inv_ell;
         gyd[j] = gC[j];
       }
+    } else if (valid && a.loss) {
+      // no evaluated sample: the pixel is the background, with no gradient
+      float e2 = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        const float e = g.bg[j] - __ldg(a.target + 3 * rid + j);
+        e2 = fmaf(e, e, e2);
+      }
+      l_rgb += sqrtf(e2 + 1e-6f);
     }
     // smoothness evaluations (Eqs. 9-10): each one is backpropagated and staged
     const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -599,11 +612,14 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
         float sh[3] = {sv[0] / sn, sv[1] / sn, sv[2] / sn};
         float ys[3], gys[3];
         mlp_forward_row(sW, F, sh, row, ys);
+        float q = 0.0f;
 #pragma unroll
         for (int j = 0; j < 3; j++) {
           gys[j] = gs * a.lam_smooth * 2.0f * S * (ys[j] - yd[j]);
           gyd[j] -= gys[j];
+          q = fmaf(ys[j] - yd[j], ys[j] - yd[j], q);
         }
+        l_smooth = fmaf(S, q, l_smooth);
         mlp_backward_row(sWT, row, ys, gys, gF);
       } else {
         zero_row(row);
@@ -625,6 +641,29 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
       float4* sv = reinterpret_cast<float4*>(a.saved + (long)kSavedFloats * rid);
       sv[3] = make_float4(gF[0], gF[1], gF[2], gF[3]);
       sv[4] = make_float4(gF[4], gF[5], gF[6], gT);
+    }
+  }
+  // loss terms of a fused step: warp sums -> CTA sum -> one global add per CTA
+  if (a.loss) {
+    __shared__ float sL[2][kBwdThreads / 32];
+    l_rgb = warp_sum(l_rgb);
+    l_smooth = warp_sum(l_smooth);
+    if (lane == 0) {
+      sL[0][warp] = l_rgb;
+      sL[1][warp] = l_smooth;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float s0 = 0.0f, s1 = 0.0f;
+      for (int w = 0; w < kBwdThreads / 32; w++) {
+        s0 += sL[0][w];
+        s1 += sL[1][w];
+      }
+      s0 *= a.lam_rgb;
+      s1 *= a.lam_smooth;
+      atomicAdd(a.loss + 1, s0);
+      atomicAdd(a.loss + 2, s1);
+      atomicAdd(a.loss + 0, s0 + s1);
     }
   }
   // weight gradients: per-warp sums (in the staging area, no longer needed)
@@ -719,8 +758,9 @@ static cudaError_t launch_mlp_bwd(const omerf_scene* s, const BwdArgs& a, cudaSt
 cudaError_t launch_march_bwd(const omerf_scene* s, const float* rays, const float* target, const float* dirs,
                              long n, int K, const float lam[3], float* saved, const float* grad_scale,
                              float* g_grid, float* g_xy, float* g_xz, float* g_yz, float* g_occ, float* g_mlp,
-                             cudaStream_t stream) {
+                             float* loss, cudaStream_t stream) {
   BwdArgs a{};
+  a.loss = loss;
   a.rays = rays;
   a.target = target;
   a.dirs = dirs;

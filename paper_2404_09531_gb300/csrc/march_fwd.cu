@@ -132,7 +132,10 @@ struct FwdArgs {
 #define OMERF_FWD_MINB 3  // resident CTAs per SM the register budget is sized for
 #endif
 
-template <class FT, bool SPARSE, bool TRAIN>
+// TRAIN: write the per-ray state the backward needs instead of pixels; with
+// LOSS also evaluate the deferred MLP and the loss terms (a fused training
+// step leaves the loss to the MLP backward, which evaluates the MLP anyway).
+template <class FT, bool SPARSE, bool TRAIN, bool LOSS>
 __global__ void __launch_bounds__(kThreads, OMERF_FWD_MINB) march_fwd_kernel(const Geo g, const FwdArgs a) {
   // BF16 render: deferred MLP on tensor cores; otherwise FP32 on CUDA cores
   constexpr bool kMMA = std::is_same<FT, __nv_bfloat16>::value && !TRAIN;
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, OMERF_FWD_MINB) march_fwd_kernel(con
       mlp_stage_row(ws.u.m, lane, valid && cnt > 0, F, d);
       mlp_bf16_warp(sFrag, ws.u.m, lane, yd_mma);
     }
-    if (valid) {
+    if (valid && (!TRAIN || LOSS)) {
       float out[3], yd[3] = {0.0f, 0.0f, 0.0f};
       if (cnt == 0) {
 #pragma unroll
@@ -242,15 +245,17 @@ __global__ void __launch_bounds__(kThreads, OMERF_FWD_MINB) march_fwd_kernel(con
             l_smooth = fmaf(S, q, l_smooth);
           }
         }
-        float4* sv = reinterpret_cast<float4*>(a.saved + (long)kSavedFloats * rid);
-        sv[0] = make_float4(F[0], F[1], F[2], F[3]);
-        sv[1] = make_float4(F[4], F[5], F[6], T);
-        sv[2] = make_float4(__int_as_float(cnt), __int_as_float(klo), __int_as_float(khi), 0.0f);
       }
+    }
+    if (TRAIN && valid) {
+      float4* sv = reinterpret_cast<float4*>(a.saved + (long)kSavedFloats * rid);
+      sv[0] = make_float4(F[0], F[1], F[2], F[3]);
+      sv[1] = make_float4(F[4], F[5], F[6], T);
+      sv[2] = make_float4(__int_as_float(cnt), __int_as_float(klo), __int_as_float(khi), 0.0f);
     }
   }
 
-  if (TRAIN) {
+  if (TRAIN && LOSS) {
     l_rgb = warp_sum(l_rgb);
     l_smooth = warp_sum(l_smooth);
     if (lane == 0) {
@@ -280,9 +285,9 @@ int persistent_blocks(const void* kernel, int threads, size_t smem, int num_sms)
   return per_sm * num_sms;
 }
 
-template <class FT, bool SPARSE, bool TRAIN>
+template <class FT, bool SPARSE, bool TRAIN, bool LOSS = TRAIN>
 static cudaError_t launch_variant(const omerf_scene* s, const FwdArgs& a, cudaStream_t stream) {
-  auto kern = march_fwd_kernel<FT, SPARSE, TRAIN>;
+  auto kern = march_fwd_kernel<FT, SPARSE, TRAIN, LOSS>;
   static int blocks[64] = {0};
   const int dev = s->device & 63;
   if (blocks[dev] == 0) blocks[dev] = persistent_blocks((const void*)kern, kThreads, 0, s->num_sms);
@@ -324,10 +329,16 @@ cudaError_t launch_march_fwd(const omerf_scene* s, const Cam* cam, const float* 
   a.counter = next_counter(s, stream);
   const bool bf16 = s->desc.feat_dtype == OMERF_BF16;
   const bool sparse = s->desc.brick > 0;
-  if (train) {
+  if (train && loss) {
     if (bf16) return sparse ? launch_variant<__nv_bfloat16, true, true>(s, a, stream)
                             : launch_variant<__nv_bfloat16, false, true>(s, a, stream);
     return sparse ? launch_variant<float, true, true>(s, a, stream) : launch_variant<float, false, true>(s, a, stream);
+  }
+  if (train) {
+    if (bf16) return sparse ? launch_variant<__nv_bfloat16, true, true, false>(s, a, stream)
+                            : launch_variant<__nv_bfloat16, false, true, false>(s, a, stream);
+    return sparse ? launch_variant<float, true, true, false>(s, a, stream)
+                  : launch_variant<float, false, true, false>(s, a, stream);
   }
   if (bf16) return sparse ? launch_variant<__nv_bfloat16, true, false>(s, a, stream)
                           : launch_variant<__nv_bfloat16, false, false>(s, a, stream);

@@ -606,7 +606,7 @@ omerf_status omerf_train_bwd(const omerf_scene* s, const float* rays, const floa
   cudaError_t e;
   if (n > 0) {
     e = launch_march_bwd(s, rays, target, smooth_dirs, n, K, lambda, static_cast<float*>(saved), grad_scale,
-                         g_grid, g_xy, g_xz, g_yz, g_occ, g_mlp, cs);
+                         g_grid, g_xy, g_xz, g_yz, g_occ, g_mlp, nullptr, cs);
     if (e != cudaSuccess) return cuda_fail(e, "train backward launch");
   }
   if (g_occ) {
@@ -622,10 +622,33 @@ omerf_status omerf_train_bwd(const omerf_scene* s, const float* rays, const floa
 omerf_status omerf_train_step(const omerf_scene* s, const float* rays, const float* target, const float* smooth_dirs,
                               int64_t n, int32_t K, const float lambda[3], void* saved, float* loss, float* g_grid,
                               float* g_xy, float* g_xz, float* g_yz, float* g_occ, float* g_mlp, void* stream) {
-  omerf_status st = omerf_train_fwd(s, rays, target, smooth_dirs, n, K, lambda, saved, loss, stream);
+  // The forward only marches and saves the per-ray state; the MLP backward,
+  // which evaluates the deferred MLP anyway, adds the Charbonnier and
+  // smoothness terms to the loss, and one L_occ launch adds its loss and
+  // gradient.
+  omerf_status st = check_train_args(s, rays, target, smooth_dirs, n, K, lambda, saved);
   if (st != OMERF_OK) return st;
-  return omerf_train_bwd(s, rays, target, smooth_dirs, n, K, lambda, saved, nullptr, g_grid, g_xy, g_xz, g_yz,
-                         g_occ, g_mlp, stream);
+  if (!loss) { set_error("loss is NULL"); return OMERF_EINVAL; }
+  const void* gps[] = {g_grid, g_xy, g_xz, g_yz};
+  for (const void* p : gps)
+    if (p && !aligned(p, 16)) { set_error("gradient buffers must be 16-byte aligned"); return OMERF_EINVAL; }
+  if (g_occ && !aligned(g_occ, 8)) { set_error("g_occ must be 8-byte aligned"); return OMERF_EINVAL; }
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(loss, 0, 4 * sizeof(float), cs);
+  if (e != cudaSuccess) return cuda_fail(e, "loss memset");
+  if (n > 0) {
+    e = launch_march_fwd(s, nullptr, rays, n, nullptr, nullptr, target, smooth_dirs, K, lambda,
+                         static_cast<float*>(saved), nullptr, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "train forward launch");
+    e = launch_march_bwd(s, rays, target, smooth_dirs, n, K, lambda, static_cast<float*>(saved), nullptr, g_grid,
+                         g_xy, g_xz, g_yz, g_occ, g_mlp, loss, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "train backward launch");
+  }
+  const long cells = (long)s->desc.occ_res * s->desc.occ_res;
+  occ_loss_kernel<<<(unsigned)std::min<long>((cells + 255) / 256, 1024), 256, 0, cs>>>(
+      s->geo.occ, cells, lambda[2], nullptr, loss, reinterpret_cast<float2*>(g_occ));
+  e = cudaGetLastError();
+  return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "occupancy loss launch");
 }
 
 omerf_status omerf_sync(void* stream, int32_t timeout_ms) {
