@@ -54,113 +54,72 @@ struct BwdArgs {
   unsigned* counter;
 };
 
-// Transposed copies of W3, W2 and the first 7 columns of W1 (the weights the
-// backward reads column-wise), 16-byte aligned rows.
-constexpr int kT3 = 0, kT2 = 64, kT1 = 320, kSmemT = 432;
+// ---------------------------------------------------------------------------
+// The per-ray deferred MLP of the backward, forward and backward, as
+// warp-level products on tensor cores: the warp's 32 rays are the rows of
+// every product (two m16 tiles), so each layer is one [32 x K] x [K x N]
+// product, run as mma.sync m16n8k8 TF32 with split operands (about FP32
+// accurate, see mma3).  Activations and deltas pass between layers through
+// the staged rows, which the weight-gradient products read afterwards.
+//
+// B fragments of the weights, per lane (b0, b1) = (B[t][g], B[t + 4][g]) of
+// each k8 x n8 block, g = lane / 4, t = lane % 4:
+//   L1  [input][unit]  = W1[unit][input]    5 k-blocks x 2 n-blocks
+//   L2  [unit1][unit2] = W2[unit2][unit1]   2 x 2
+//   B2  [unit2][unit1] = W2[unit2][unit1]   2 x 2   (g1 = G2 . W2)
+//   B1  [unit1][input] = W1[unit1][input]   2 x 1   (dL/dF = G1 . W1[:, :7])
+// W3 (3 x 16) is read from a compact copy.
+constexpr int kFragL1 = 0, kFragL2 = 10, kFragB2 = 14, kFragB1 = 18, kFrags = 20;
 
-__device__ __forceinline__ void load_mlp_transposed(const float* __restrict__ gw, float* __restrict__ st) {
-  for (int i = threadIdx.x; i < kSmemT; i += blockDim.x) {
-    float v = 0.0f;
-    if (i < kT2) {
-      const int r = i >> 2, c = i & 3;  // W3T[r][c] = W3[c][r], c < 3
-      v = c < 3 ? gw[kOffW3 + c * 16 + r] : 0.0f;
-    } else if (i < kT1) {
-      const int r = (i - kT2) >> 4, c = (i - kT2) & 15;  // W2T[r][c] = W2[c][r]
-      v = gw[kOffW2 + c * 16 + r];
+struct MlpBwdShared {
+  float2 frag[kFrags][32];
+  float w3[48];
+  float b1[16], b2[16], b3[4];
+};
+
+__device__ __forceinline__ void build_bwd_frags(const float* __restrict__ gw, MlpBwdShared& S) {
+  for (int i = threadIdx.x; i < kFrags * 32; i += blockDim.x) {
+    const int f = i >> 5, l = i & 31, g = l >> 2, t = l & 3;
+    float v0, v1;
+    if (f < kFragL2) {
+      const int s = f >> 1, j = f & 1, u = 8 * j + g, c0 = 8 * s + t, c1 = c0 + 4;
+      v0 = c0 < 34 ? gw[kOffW1 + u * 34 + c0] : 0.0f;
+      v1 = c1 < 34 ? gw[kOffW1 + u * 34 + c1] : 0.0f;
+    } else if (f < kFragB2) {
+      const int s = (f - kFragL2) >> 1, j = (f - kFragL2) & 1, u2 = 8 * j + g;
+      v0 = gw[kOffW2 + u2 * 16 + 8 * s + t];
+      v1 = gw[kOffW2 + u2 * 16 + 8 * s + t + 4];
+    } else if (f < kFragB1) {
+      const int s = (f - kFragB2) >> 1, j = (f - kFragB2) & 1, u1 = 8 * j + g;
+      v0 = gw[kOffW2 + (8 * s + t) * 16 + u1];
+      v1 = gw[kOffW2 + (8 * s + t + 4) * 16 + u1];
     } else {
-      const int r = (i - kT1) >> 4, c = (i - kT1) & 15;  // W1T[r][c] = W1[c][r], r < 7
-      v = gw[kOffW1 + c * 34 + r];
+      const int s = f - kFragB1;
+      v0 = g < 7 ? gw[kOffW1 + (8 * s + t) * 34 + g] : 0.0f;
+      v1 = g < 7 ? gw[kOffW1 + (8 * s + t + 4) * 34 + g] : 0.0f;
     }
-    st[i] = v;
+    S.frag[f][l] = make_float2(v0, v1);
+  }
+  for (int i = threadIdx.x; i < 48 + 36; i += blockDim.x) {
+    if (i < 48) S.w3[i] = gw[kOffW3 + i];
+    else if (i < 64) S.b1[i - 48] = gw[kOffB1 + i - 48];
+    else if (i < 80) S.b2[i - 64] = gw[kOffB2 + i - 64];
+    else S.b3[i - 80] = i - 80 < 3 ? gw[kOffB3 + i - 80] : 0.0f;
   }
 }
 
-// Deferred MLP forward for one lane's ray from the padded weights, writing
-// the staged row (x, h1 = relu(a1), h2 = relu(a2)); returns y.
-__device__ __forceinline__ void mlp_forward_row(const float* __restrict__ W, const float F[7], const float d[3],
-                                                float* __restrict__ row, float y[3]) {
-  float x[36];
+// This lane's staged input row [F (7), view encoding (27)], zeros if !live.
+__device__ __forceinline__ void stage_x(float* __restrict__ row, bool live, const float F[7], const float d[3]) {
+  float x[34];
 #pragma unroll
-  for (int i = 0; i < 7; i++) x[i] = F[i];
-  view_encoding(d, x + 7);
-  x[34] = 0.0f;
-  x[35] = 0.0f;
+  for (int i = 0; i < 34; i++) x[i] = 0.0f;
+  if (live) {
+#pragma unroll
+    for (int i = 0; i < 7; i++) x[i] = F[i];
+    view_encoding(d, x + 7);
+  }
 #pragma unroll
   for (int i = 0; i < 34; i++) row[i] = x[i];
-  float h1[16];
-#pragma unroll
-  for (int j = 0; j < 16; j++) {
-    const float4* w = reinterpret_cast<const float4*>(W + kSW1 + 36 * j);
-    float a = W[kSB1 + j];
-#pragma unroll
-    for (int q = 0; q < 9; q++) a = dot4(w[q], x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3], a);
-    h1[j] = fmaxf(a, 0.0f);
-    row[34 + j] = h1[j];
-  }
-  float h2[16];
-#pragma unroll
-  for (int j = 0; j < 16; j++) {
-    const float4* w = reinterpret_cast<const float4*>(W + kSW2 + 16 * j);
-    float a = W[kSB2 + j];
-#pragma unroll
-    for (int q = 0; q < 4; q++) a = dot4(w[q], h1[4 * q], h1[4 * q + 1], h1[4 * q + 2], h1[4 * q + 3], a);
-    h2[j] = fmaxf(a, 0.0f);
-    row[50 + j] = h2[j];
-  }
-#pragma unroll
-  for (int j = 0; j < 3; j++) {
-    const float4* w = reinterpret_cast<const float4*>(W + kSW3 + 16 * j);
-    float a = W[kSB3 + j];
-#pragma unroll
-    for (int q = 0; q < 4; q++) a = dot4(w[q], h2[4 * q], h2[4 * q + 1], h2[4 * q + 2], h2[4 * q + 3], a);
-    y[j] = sigmoidf_(a);
-  }
-}
-
-// Backprop gy through the staged evaluation with the transposed weights:
-// writes the layer deltas (g1, g2, g3) into the row and adds the
-// feature-input gradient into gF.  A ReLU unit is active iff its staged
-// output is positive.
-__device__ __forceinline__ void mlp_backward_row(const float* __restrict__ WT, float* __restrict__ row,
-                                                 const float y[3], const float gy[3], float gF[7]) {
-  float g3[4];
-#pragma unroll
-  for (int j = 0; j < 3; j++) {
-    g3[j] = gy[j] * y[j] * (1.0f - y[j]);
-    row[98 + j] = g3[j];
-  }
-  g3[3] = 0.0f;
-  float g2[16];
-#pragma unroll
-  for (int i = 0; i < 16; i++) {
-    const float4 w = *reinterpret_cast<const float4*>(WT + kT3 + 4 * i);
-    const float a = dot4(w, g3[0], g3[1], g3[2], g3[3], 0.0f);
-    g2[i] = row[50 + i] > 0.0f ? a : 0.0f;
-    row[82 + i] = g2[i];
-  }
-  float g1[16];
-#pragma unroll
-  for (int i = 0; i < 16; i++) {
-    const float4* w = reinterpret_cast<const float4*>(WT + kT2 + 16 * i);
-    float a = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 4; q++) a = dot4(w[q], g2[4 * q], g2[4 * q + 1], g2[4 * q + 2], g2[4 * q + 3], a);
-    g1[i] = row[34 + i] > 0.0f ? a : 0.0f;
-    row[66 + i] = g1[i];
-  }
-#pragma unroll
-  for (int i = 0; i < 7; i++) {
-    const float4* w = reinterpret_cast<const float4*>(WT + kT1 + 16 * i);
-    float a = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 4; q++) a = dot4(w[q], g1[4 * q], g1[4 * q + 1], g1[4 * q + 2], g1[4 * q + 3], a);
-    gF[i] += a;
-  }
-}
-
-__device__ __forceinline__ void zero_row(float* __restrict__ row) {
-#pragma unroll 4
-  for (int i = 0; i < kRow; i++) row[i] = 0.0f;
 }
 
 // ---------------------------------------------------------------------------
@@ -294,6 +253,208 @@ __device__ __forceinline__ void store_acc(const DwAcc& acc, int lane, float* __r
       }
     }
   }
+}
+
+// Split the A fragment (rows r0 / r1 = m-tile rows g / g + 8, columns c0 and
+// c0 + 4 of the staged rows, zero where the column is not valid).
+__device__ __forceinline__ void load_a(const float* r0, const float* r1, int c0, bool v0, bool v1, uint32_t ah[4],
+                                       uint32_t al[4]) {
+  split_tf32(v0 ? r0[c0] : 0.0f, ah[0], al[0]);
+  split_tf32(v0 ? r1[c0] : 0.0f, ah[1], al[1]);
+  split_tf32(v1 ? r0[c0 + 4] : 0.0f, ah[2], al[2]);
+  split_tf32(v1 ? r1[c0 + 4] : 0.0f, ah[3], al[3]);
+}
+
+// G for the warp's 32 staged rows (x in columns 0..33): writes h1 (34..49),
+// h2 (50..65) and this lane's sigmoid outputs y.  All 32 lanes call it.
+__device__ __forceinline__ void warp_mlp_forward(float* __restrict__ rows, const MlpBwdShared& S, int lane,
+                                                 float y[3]) {
+  __syncwarp();
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+  for (int mt = 0; mt < 2; mt++) {
+    float* r0 = rows + (16 * mt + g) * kRow;
+    float* r1 = r0 + 8 * kRow;
+    float c[2][4];
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      c[j][0] = c[j][2] = S.b1[8 * j + 2 * t];
+      c[j][1] = c[j][3] = S.b1[8 * j + 2 * t + 1];
+    }
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+      uint32_t ah[4], al[4];
+      load_a(r0, r1, 8 * s + t, 8 * s + t < 34, 8 * s + t + 4 < 34, ah, al);
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        const float2 b = S.frag[kFragL1 + 2 * s + j][lane];
+        mma3(c[j], ah, al, b.x, b.y);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const int u = 34 + 8 * j + 2 * t;
+      r0[u] = fmaxf(c[j][0], 0.0f);
+      r0[u + 1] = fmaxf(c[j][1], 0.0f);
+      r1[u] = fmaxf(c[j][2], 0.0f);
+      r1[u + 1] = fmaxf(c[j][3], 0.0f);
+    }
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int mt = 0; mt < 2; mt++) {
+    float* r0 = rows + (16 * mt + g) * kRow;
+    float* r1 = r0 + 8 * kRow;
+    float c[2][4];
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      c[j][0] = c[j][2] = S.b2[8 * j + 2 * t];
+      c[j][1] = c[j][3] = S.b2[8 * j + 2 * t + 1];
+    }
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      uint32_t ah[4], al[4];
+      load_a(r0, r1, 34 + 8 * s + t, true, true, ah, al);
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        const float2 b = S.frag[kFragL2 + 2 * s + j][lane];
+        mma3(c[j], ah, al, b.x, b.y);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const int u = 50 + 8 * j + 2 * t;
+      r0[u] = fmaxf(c[j][0], 0.0f);
+      r0[u + 1] = fmaxf(c[j][1], 0.0f);
+      r1[u] = fmaxf(c[j][2], 0.0f);
+      r1[u + 1] = fmaxf(c[j][3], 0.0f);
+    }
+  }
+  __syncwarp();
+  // layer 3: B[k = unit2][n = output] = W3[output][unit2], outputs 0..2 of 8
+#pragma unroll 1
+  for (int mt = 0; mt < 2; mt++) {
+    float* r0 = rows + (16 * mt + g) * kRow;
+    float* r1 = r0 + 8 * kRow;
+    float c[4];
+    c[0] = c[2] = 2 * t < 3 ? S.b3[2 * t] : 0.0f;
+    c[1] = c[3] = 2 * t + 1 < 3 ? S.b3[2 * t + 1] : 0.0f;
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      uint32_t ah[4], al[4];
+      load_a(r0, r1, 50 + 8 * s + t, true, true, ah, al);
+      const float b0 = g < 3 ? S.w3[g * 16 + 8 * s + t] : 0.0f;
+      const float b1 = g < 3 ? S.w3[g * 16 + 8 * s + t + 4] : 0.0f;
+      mma3(c, ah, al, b0, b1);
+    }
+    // pre-activations into the g3 columns (this lane's row is read back below)
+    if (2 * t < 3) {
+      r0[98 + 2 * t] = c[0];
+      r1[98 + 2 * t] = c[2];
+    }
+    if (2 * t + 1 < 3) {
+      r0[98 + 2 * t + 1] = c[1];
+      r1[98 + 2 * t + 1] = c[3];
+    }
+  }
+  __syncwarp();
+  const float* row = rows + lane * kRow;
+#pragma unroll
+  for (int j = 0; j < 3; j++) y[j] = sigmoidf_(row[98 + j]);
+}
+
+// Backpropagate this lane's gy through the staged evaluation: writes the
+// deltas g3 (98..100), g2 (82..97) and g1 (66..81).  A ReLU unit is active
+// iff its staged output is positive.  All 32 lanes call it.
+__device__ __forceinline__ void warp_mlp_backward(float* __restrict__ rows, const MlpBwdShared& S, int lane,
+                                                  const float y[3], const float gy[3]) {
+  const int g = lane >> 2, t = lane & 3;
+  {
+    float* row = rows + lane * kRow;
+#pragma unroll
+    for (int j = 0; j < 3; j++) row[98 + j] = gy[j] * y[j] * (1.0f - y[j]);
+  }
+  __syncwarp();
+  // g2 = (G3 . W3) masked: K = 3 outputs (one k8 block, rows t < 3)
+#pragma unroll 1
+  for (int mt = 0; mt < 2; mt++) {
+    float* r0 = rows + (16 * mt + g) * kRow;
+    float* r1 = r0 + 8 * kRow;
+    uint32_t ah[4], al[4];
+    load_a(r0, r1, 98 + t, t < 3, false, ah, al);
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      const float b0 = t < 3 ? S.w3[t * 16 + 8 * j + g] : 0.0f;
+      mma3(c, ah, al, b0, 0.0f);
+      const int u = 8 * j + 2 * t;
+      r0[82 + u] = r0[50 + u] > 0.0f ? c[0] : 0.0f;
+      r0[83 + u] = r0[51 + u] > 0.0f ? c[1] : 0.0f;
+      r1[82 + u] = r1[50 + u] > 0.0f ? c[2] : 0.0f;
+      r1[83 + u] = r1[51 + u] > 0.0f ? c[3] : 0.0f;
+    }
+  }
+  __syncwarp();
+  // g1 = (G2 . W2) masked
+#pragma unroll 1
+  for (int mt = 0; mt < 2; mt++) {
+    float* r0 = rows + (16 * mt + g) * kRow;
+    float* r1 = r0 + 8 * kRow;
+    float c[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      uint32_t ah[4], al[4];
+      load_a(r0, r1, 82 + 8 * s + t, true, true, ah, al);
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        const float2 b = S.frag[kFragB2 + 2 * s + j][lane];
+        mma3(c[j], ah, al, b.x, b.y);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const int u = 8 * j + 2 * t;
+      r0[66 + u] = r0[34 + u] > 0.0f ? c[j][0] : 0.0f;
+      r0[67 + u] = r0[35 + u] > 0.0f ? c[j][1] : 0.0f;
+      r1[66 + u] = r1[34 + u] > 0.0f ? c[j][2] : 0.0f;
+      r1[67 + u] = r1[35 + u] > 0.0f ? c[j][3] : 0.0f;
+    }
+  }
+  __syncwarp();
+}
+
+// dL/dF = G1 . W1[:, :7] for the warp's rows, added into this lane's gF.
+// Uses the x columns 0..6 as scratch: call after the weight-gradient products.
+__device__ __forceinline__ void warp_mlp_input_grad(float* __restrict__ rows, const MlpBwdShared& S, int lane,
+                                                    float gF[7]) {
+  __syncwarp();
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+  for (int mt = 0; mt < 2; mt++) {
+    float* r0 = rows + (16 * mt + g) * kRow;
+    float* r1 = r0 + 8 * kRow;
+    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      uint32_t ah[4], al[4];
+      load_a(r0, r1, 66 + 8 * s + t, true, true, ah, al);
+      const float2 b = S.frag[kFragB1 + s][lane];
+      mma3(c, ah, al, b.x, b.y);
+    }
+    __syncwarp();  // every lane has read its g1 columns of these rows
+    if (2 * t < 7) {
+      r0[2 * t] = c[0];
+      r1[2 * t] = c[2];
+    }
+    if (2 * t + 1 < 7) {
+      r0[2 * t + 1] = c[1];
+      r1[2 * t + 1] = c[3];
+    }
+  }
+  __syncwarp();
+  const float* row = rows + lane * kRow;
+#pragma unroll
+  for (int i = 0; i < 7; i++) gF[i] += row[i];
 }
 
 // Scatter w * dt to the texel at element offset `off`, first summing runs of
@@ -543,12 +704,10 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
 __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, const BwdArgs a) {
   extern __shared__ float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* sW = smem;                                   // padded MLP weights
-  float* sWT = smem + kSmemMlp;                       // transposed weights for the backward
-  float* rowsAll = smem + kSmemMlp + kSmemT;          // 32 staged rows per warp
+  MlpBwdShared& S = *reinterpret_cast<MlpBwdShared*>(smem);
+  float* rowsAll = smem + sizeof(MlpBwdShared) / sizeof(float);  // 32 staged rows per warp
   float* rows = rowsAll + warp * 32 * kRow;
-  load_mlp_padded(g.mlp, sW);
-  load_mlp_transposed(g.mlp, sWT);
+  build_bwd_frags(g.mlp, S);
   __syncthreads();
   const float gs = a.grad_scale ? __ldg(a.grad_scale) : 1.0f;
   const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
@@ -575,8 +734,9 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
     float* row = rows + lane * kRow;
     float gF[7] = {0, 0, 0, 0, 0, 0, 0};
     float gC[3] = {0, 0, 0}, yd[3] = {0, 0, 0}, gyd[3] = {0, 0, 0};
+    stage_x(row, live, F, d);
+    warp_mlp_forward(rows, S, lane, yd);
     if (live) {
-      mlp_forward_row(sW, F, d, row, yd);
       float e[3], e2 = 0.0f;
 #pragma unroll
       for (int j = 0; j < 3; j++) {
@@ -604,36 +764,39 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
     // smoothness evaluations (Eqs. 9-10): each one is backpropagated and staged
     const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     for (int k = 0; k < a.K; k++) {
+      float sh[3] = {0.0f, 0.0f, 1.0f}, S_cos = 0.0f;
       if (live) {
         const float* sp = a.dirs + 3 * ((long)rid * a.K + k);
         float sv[3] = {__ldg(sp), __ldg(sp + 1), __ldg(sp + 2)};
         const float sn = sqrtf(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
-        const float S = (d[0] * sv[0] + d[1] * sv[1] + d[2] * sv[2]) / (dn * sn);
-        float sh[3] = {sv[0] / sn, sv[1] / sn, sv[2] / sn};
-        float ys[3], gys[3];
-        mlp_forward_row(sW, F, sh, row, ys);
+        S_cos = (d[0] * sv[0] + d[1] * sv[1] + d[2] * sv[2]) / (dn * sn);
+#pragma unroll
+        for (int c = 0; c < 3; c++) sh[c] = sv[c] / sn;
+      }
+      stage_x(row, live, F, sh);
+      float ys[3], gys[3] = {0.0f, 0.0f, 0.0f};
+      warp_mlp_forward(rows, S, lane, ys);
+      if (live) {
         float q = 0.0f;
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-          gys[j] = gs * a.lam_smooth * 2.0f * S * (ys[j] - yd[j]);
+          gys[j] = gs * a.lam_smooth * 2.0f * S_cos * (ys[j] - yd[j]);
           gyd[j] -= gys[j];
           q = fmaf(ys[j] - yd[j], ys[j] - yd[j], q);
         }
-        l_smooth = fmaf(S, q, l_smooth);
-        mlp_backward_row(sWT, row, ys, gys, gF);
-      } else {
-        zero_row(row);
+        l_smooth = fmaf(S_cos, q, l_smooth);
       }
+      warp_mlp_backward(rows, S, lane, ys, gys);
       if (want_dw) accumulate_mma(rows, lane, acc);
+      warp_mlp_input_grad(rows, S, lane, gF);
     }
-    if (live) {
-      float y[3];
-      mlp_forward_row(sW, F, d, row, y);
-      mlp_backward_row(sWT, row, y, gyd, gF);
-    } else {
-      zero_row(row);
-    }
+    // the evaluation at d, recomputed (the smoothness evaluations reused the rows)
+    float y[3];
+    stage_x(row, live, F, d);
+    warp_mlp_forward(rows, S, lane, y);
+    warp_mlp_backward(rows, S, lane, y, gyd);
     if (want_dw) accumulate_mma(rows, lane, acc);
+    warp_mlp_input_grad(rows, S, lane, gF);
     if (valid) {
 #pragma unroll
       for (int j = 0; j < 3; j++) gF[j] += gC[j];
@@ -741,7 +904,7 @@ static cudaError_t launch_bwd_variant(const omerf_scene* s, const BwdArgs& a, cu
 }
 
 static cudaError_t launch_mlp_bwd(const omerf_scene* s, const BwdArgs& a, cudaStream_t stream) {
-  const size_t smem = (size_t)(kSmemMlp + kSmemT + (kBwdThreads / 32) * 32 * kRow) * sizeof(float);
+  const size_t smem = sizeof(MlpBwdShared) + (size_t)(kBwdThreads / 32) * 32 * kRow * sizeof(float);
   static int blocks[64] = {0};
   const int dev = s->device & 63;
   if (blocks[dev] == 0) {
