@@ -21,17 +21,8 @@
 namespace omerf {
 
 constexpr int kBwdThreads = 128;   // 4 warps per CTA
-#ifndef OMERF_PAIR_FOLD
-#define OMERF_PAIR_FOLD 1  // fold neighbouring lanes that share a whole stencil
-#endif
 #ifndef OMERF_FOLD
 #define OMERF_FOLD 3       // lanes folded into one reduction
-#endif
-#ifndef OMERF_RUN_GRID
-#define OMERF_RUN_GRID 1   // otherwise: grid-corner runs folded over up to 2^1 lanes
-#endif
-#ifndef OMERF_RUN_PLANE
-#define OMERF_RUN_PLANE 1  // and plane-texel runs over up to 2^1 lanes
 #endif
 constexpr int kRow = 101;          // staged floats per ray: x 34, h1 16, h2 16, g1 16, g2 16, g3 3
 
@@ -457,40 +448,6 @@ __device__ __forceinline__ void warp_mlp_input_grad(float* __restrict__ rows, co
   for (int i = 0; i < 7; i++) gF[i] += row[i];
 }
 
-// Scatter w * dt to the texel at element offset `off`, first summing runs of
-// neighbouring lanes that hit the same texel (consecutive samples of a ray
-// often share a grid corner or plane texel): lanes [l, l + 2^STEPS) of a run
-// are folded into lane l, so one pair of vector reductions is issued per
-// chunk of the run instead of one per sample.  All 32 lanes must call it.
-template <int STEPS>
-__device__ __forceinline__ void scatter8_runs(float* base, int off, float w, const float dt[8], bool valid,
-                                              int lane) {
-  const int key = valid ? off : -1 - lane;
-  const int kprev = __shfl_up_sync(kFull, key, 1);
-  const unsigned H = __ballot_sync(kFull, lane == 0 || kprev != key);
-  const int runstart = 31 - __clz(H & lanemask_le());
-  const unsigned later = H & ~lanemask_le();
-  const int runend = later ? __ffs(later) - 1 : 32;
-  float v[8];
-#pragma unroll
-  for (int c = 0; c < 8; c++) v[c] = valid ? w * dt[c] : 0.0f;
-#pragma unroll
-  for (int st = 0; st < STEPS; st++) {
-    const int dd = 1 << st;
-    const bool take = lane + dd < runend;
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-      const float u = __shfl_down_sync(kFull, v[c], dd);
-      if (take) v[c] += u;
-    }
-  }
-  if (valid && ((lane - runstart) & ((1 << STEPS) - 1)) == 0) {
-    float4* q = reinterpret_cast<float4*>(base + off);
-    atomicAdd(q, make_float4(v[0], v[1], v[2], v[3]));
-    atomicAdd(q + 1, make_float4(v[4], v[5], v[6], v[7]));
-  }
-}
-
 // Pair folding by stencil: lanes whose samples share the key (the base grid
 // vertex, or a plane's base texel) share every texel of that stencil, so a
 // lane at an even position of a run of equal keys adds its right neighbour's
@@ -509,12 +466,6 @@ __device__ __forceinline__ void red8(float* base, int off, const float v[8]) {
   float4* q = reinterpret_cast<float4*>(base + off);
   atomicAdd(q, make_float4(v[0], v[1], v[2], v[3]));
   atomicAdd(q + 1, make_float4(v[4], v[5], v[6], v[7]));
-}
-
-__device__ __forceinline__ void scatter8(float* base, int off, float w, const float dt[8]) {
-  float4* q = reinterpret_cast<float4*>(base + off);
-  atomicAdd(q, make_float4(w * dt[0], w * dt[1], w * dt[2], w * dt[3]));
-  atomicAdd(q + 1, make_float4(w * dt[4], w * dt[5], w * dt[6], w * dt[7]));
 }
 
 // Per-warp shared state of the packed backward re-march of 32 rays.
@@ -621,7 +572,6 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
       }
     }
     // gradient scatter (all lanes; inactive lanes contribute nothing)
-#if OMERF_PAIR_FOLD
     // neighbours' dL/dt and weights, lanes +1 .. +OMERF_FOLD-1
     float dtn[OMERF_FOLD - 1][8];
 #pragma unroll
@@ -671,21 +621,6 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
         }
       }
     }
-#else
-    if (a.g_grid) {
-#pragma unroll
-      for (int c = 0; c < 8; c++) scatter8_runs<OMERF_RUN_GRID>(a.g_grid, goff[c], gw[c], dt, act && goff[c] >= 0, lane);
-    }
-    {
-      float* gp[3] = {a.g_xy, a.g_xz, a.g_yz};
-#pragma unroll
-      for (int q = 0; q < 3; q++) {
-        if (!gp[q]) continue;
-#pragma unroll
-        for (int c = 0; c < 4; c++) scatter8_runs<OMERF_RUN_PLANE>(gp[q], poff[4 * q + c], pw[4 * q + c], dt, act, lane);
-      }
-    }
-#endif
     const int rnext = __shfl_down_sync(kFull, r, 1);
     const bool tail = act && (lane == 31 || rnext != r);
     __syncwarp();
