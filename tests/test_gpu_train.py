@@ -155,3 +155,68 @@ def test_bf16_features_train_against_rounded_oracle():
     torch.cuda.synchronize()
     ref = oracle.train(oracle.OracleScene(sc_b), batch["rays"], batch["target"], batch["smooth_dirs"], lam=LAM)
     _check_grads(res, ref, what="bf16")
+
+
+def _view_encoding(d):
+    parts = [d]
+    for k in range(4):
+        parts += [np.sin((2.0 ** k) * d), np.cos((2.0 ** k) * d)]
+    return np.concatenate(parts, 1)
+
+
+def _unambiguous(sc, batch, margin=1e-4):
+    """Drop the few rays where FP32 and FP64 may take different branches:
+    (a) the transmittance passes within 1e-4 (relative) of the termination
+    threshold at a sample (they may stop one sample apart, as in the render
+    parity), and (b) a hidden unit of an MLP evaluation of the ray (at d or
+    at a smoothness direction) has a pre-activation within `margin` of the
+    ReLU kink, where the two sides take different derivatives.  Both are a
+    fraction of a percent of the rays of a large batch."""
+    out = oracle.render(oracle.OracleScene(sc), batch["rays"])
+    amb = out["ambiguous"] != 0
+    P = np.asarray(sc["mlp"], np.float64)
+    W1, b1 = P[0:544].reshape(16, 34), P[544:560]
+    W2, b2 = P[560:816].reshape(16, 16), P[816:832]
+    d = batch["rays"][:, 3:].astype(np.float64)
+    dirs = [d] + [batch["smooth_dirs"][:, k].astype(np.float64) for k in range(batch["smooth_dirs"].shape[1])]
+    kink = np.zeros(len(d), bool)
+    for v in dirs:
+        v = v / np.linalg.norm(v, axis=1, keepdims=True)
+        a1 = np.concatenate([out["F"], _view_encoding(v)], 1) @ W1.T + b1
+        a2 = np.maximum(a1, 0.0) @ W2.T + b2
+        kink |= (np.abs(a1).min(1) < margin) | (np.abs(a2).min(1) < margin)
+    drop = amb | (kink & (out["count"] > 0))
+    assert drop.mean() < 1e-2
+    return {k: v[~drop] for k, v in batch.items()}
+
+
+def test_config3_full_batch_as_benchmarked():
+    """The benchmarked training workload at full size: 2^18 config-3 rays
+    (less the ambiguous ones),
+    K = 1, lambda = (1, 1e-2, 1e-4), one fused step through the C ABI; every
+    parameter tensor's gradient and the loss against the FP64 oracle."""
+    sc = synth.make_scene(3)
+    batch = _unambiguous(sc, synth.make_train_batch(3, 1 << 18))
+    batch["target"] = oracle.render(oracle.OracleScene(synth.perturb_scene(sc)), batch["rays"])["rgb"].astype(
+        np.float32)
+    scene, res, ref = _run(sc, batch)
+    loss = res["loss"].cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(loss[0], ref["loss"], rtol=1e-5)
+    np.testing.assert_allclose(loss[1:], ref["loss_terms"], rtol=1e-4, atol=1e-9)
+    _check_grads(res, ref, what="config 3 full")
+
+
+def test_config5_full_batch_bf16_as_benchmarked():
+    """2^20 rays of 64 cameras with BF16 features (the large precision
+    workload): gradients against the oracle on the BF16-rounded features."""
+    sc = synth.make_scene(5)
+    rb = lambda a: torch.as_tensor(a).to(torch.bfloat16).float().numpy()  # noqa: E731
+    sc_b = dict(sc, grid=rb(sc["grid"]), p_xy=rb(sc["p_xy"]), p_xz=rb(sc["p_xz"]), p_yz=rb(sc["p_yz"]))
+    batch = _unambiguous(sc_b, synth.make_train_batch(5, 1 << 20))
+    scene = gpu_scene(sc)
+    assert scene.feat_dtype == torch.bfloat16
+    res = om.train_step(scene, batch["rays"], batch["target"], batch["smooth_dirs"], lam=LAM)
+    torch.cuda.synchronize()
+    ref = oracle.train(oracle.OracleScene(sc_b), batch["rays"], batch["target"], batch["smooth_dirs"], lam=LAM)
+    np.testing.assert_allclose(float(res["loss"][0]), ref["loss"], rtol=1e-5)
+    _check_grads(res, ref, what="config 5 full bf16")
