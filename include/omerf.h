@@ -153,8 +153,13 @@ omerf_status omerf_ray_interval(const omerf_scene *scene, const omerf_camera *ca
  * and rgb = bg for a ray with no evaluated sample.
  *   cam    host camera (n == width * height, rays NULL), or NULL
  *   rays   device [n][6] float32 when cam is NULL
- *   rgb    device float32 [n][3] (output)
- *   count  device int32 [n] evaluated samples per ray (output, may be NULL)
+ *   rgb    float32 [n][3] (output): device memory, or page-locked host memory
+ *          (cudaHostAlloc / cudaHostRegister), which the kernel writes
+ *          directly (on Grace-Blackwell over the coherent chip-to-chip link),
+ *          so that no copy follows the render; any other host pointer is
+ *          rejected with OMERF_EDEVICE
+ *   count  int32 [n] evaluated samples per ray (output, may be NULL), memory
+ *          as for rgb
  * The deferred MLP runs in float32 for OMERF_F32 scenes and in bfloat16 on
  * tensor cores with float32 accumulation for OMERF_BF16 scenes. */
 omerf_status omerf_render(const omerf_scene *scene, const omerf_camera *cam, const float *rays,

@@ -285,8 +285,9 @@ def render(scene: Scene, camera=None, rays=None, out=None, count_out=None, strea
     """Forward render (Eqs. 1-4, 6-8) of a camera (dict) or of rays [n, 6].
 
     Returns (rgb [n, 3] float32, count [n] int32 or None) on the scene's
-    device.  With ``out`` (and ``count_out``) given as CPU tensors, the
-    results are copied into them (the copy is enqueued on the stream).
+    device.  With ``out`` (and ``count_out``) given as page-locked CPU
+    tensors the kernel writes the pixels straight into them; other CPU
+    tensors receive a copy enqueued on the stream.
     """
     dev = scene.device
     cam_p = None
@@ -298,9 +299,17 @@ def render(scene: Scene, camera=None, rays=None, out=None, count_out=None, strea
     else:
         rays_t = _dev_f32(rays, dev)
         n = int(rays_t.shape[0])
+    st = _stream(stream)
+    direct = out is not None and not out.is_cuda and out.is_pinned() and out.is_contiguous() and \
+        out.dtype == torch.float32 and out.numel() == 3 * n and \
+        (count_out is None or (count_out.is_pinned() and count_out.is_contiguous() and
+                               count_out.dtype == torch.int32 and count_out.numel() == n))
+    if direct:
+        _check(lib().omerf_render(scene.handle, cam_p, _ptr(rays_t), n, _ptr(out), _ptr(count_out), st),
+               "omerf_render")
+        return out, count_out
     rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
     count = torch.empty(n, dtype=torch.int32, device=dev) if (want_count or count_out is not None) else None
-    st = _stream(stream)
     _check(lib().omerf_render(scene.handle, cam_p, _ptr(rays_t), n, _ptr(rgb), _ptr(count), st), "omerf_render")
     if out is not None:
         out.copy_(rgb, non_blocking=True)

@@ -538,11 +538,38 @@ omerf_status omerf_ray_interval(const omerf_scene* s, const omerf_camera* cam, c
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "interval kernel");
 }
 
+// An output buffer of the render: device memory, or page-locked host memory
+// the device addresses directly (the pointer the device uses is returned).
+static omerf_status output_ptr(void* p, void** dev, const char* name) {
+  *dev = p;
+  if (!p) return OMERF_OK;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("%s: not a CUDA-accessible pointer", name);
+    return OMERF_EDEVICE;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return OMERF_OK;
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *dev = at.devicePointer;
+    return OMERF_OK;
+  }
+  set_error("%s must be device memory or page-locked host memory", name);
+  return OMERF_EDEVICE;
+}
+
 omerf_status omerf_render(const omerf_scene* s, const omerf_camera* cam, const float* rays, int64_t n, float* rgb,
                           int32_t* count, void* stream) {
   if (!s || (!rgb && n > 0)) { set_error("NULL argument"); return OMERF_EINVAL; }
   if (n < 0) { set_error("n must be >= 0"); return OMERF_ESHAPE; }
   omerf_status st;
+  if (n > 0) {
+    void *rd = nullptr, *cd = nullptr;
+    if ((st = output_ptr(rgb, &rd, "rgb")) != OMERF_OK) return st;
+    if ((st = output_ptr(count, &cd, "count")) != OMERF_OK) return st;
+    rgb = static_cast<float*>(rd);
+    count = static_cast<int32_t*>(cd);
+  }
   Cam k{};
   if (cam) {
     if ((st = validate_camera(cam, n)) != OMERF_OK) return st;

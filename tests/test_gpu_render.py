@@ -4,6 +4,7 @@ Bar: per-ray sample counts bit-exact (rays the oracle marks ambiguous at the
 termination threshold are excluded and counted), FP32 rgb max-abs <= 1e-4,
 BF16 PSNR >= 45 dB.
 """
+import ctypes
 import dataclasses
 
 import numpy as np
@@ -257,3 +258,29 @@ def test_sync_is_bounded():
     om.sync(timeout_ms=60000)
     lib = om.lib()
     assert lib.omerf_sync(None, 0) in (0, -5)  # an idle or busy stream: done or timed out, never blocks
+
+
+def test_render_into_page_locked_host_memory():
+    """The kernel writes rgb and counts straight into page-locked host buffers
+    (the same values as a device render); a pageable CPU tensor gets a copy;
+    a pageable pointer handed to the C ABI is rejected before any launch."""
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    cam = synth.make_cameras(1)[0]
+    n = cam["width"] * cam["height"]
+    rgb_d, cnt_d = om.render(scene, camera=cam)
+    h_rgb = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    h_cnt = torch.empty(n, dtype=torch.int32).pin_memory()
+    om.render(scene, camera=cam, out=h_rgb, count_out=h_cnt)
+    torch.cuda.synchronize()
+    assert torch.equal(h_rgb, rgb_d.cpu()) and torch.equal(h_cnt, cnt_d.cpu())
+    p_rgb = torch.empty((n, 3), dtype=torch.float32)
+    om.render(scene, camera=cam, out=p_rgb)
+    torch.cuda.synchronize()
+    assert torch.equal(p_rgb, rgb_d.cpu())
+    pageable = np.zeros((n, 3), np.float32)
+    lib = om.lib()
+    rc = lib.omerf_render(scene.handle, ctypes.byref(om.camera_struct(cam)), None, n,
+                          ctypes.c_void_p(pageable.ctypes.data), None, None)
+    assert rc == -3
+    assert b"page-locked" in lib.omerf_last_error()
