@@ -265,17 +265,18 @@ __device__ __forceinline__ void grid_stencil(const Geo& g, const float p[3], int
     // (one 256-bit read) gives the brick of every corner without branching
     const int s = g.blog2, m = (1 << s) - 1, B = 1 << s;
     const int b0 = __ldg(g.table + ((i[0] >> s) * g.nb[1] + (i[1] >> s)) * g.nb[2] + (i[2] >> s));
+    const int cx = (i[0] & m) == m, cy = (i[1] & m) == m, cz = (i[2] & m) == m;
     int nb[8];
-    if (b0 >= 0) {
+    if (b0 >= 0 && (cx | cy | cz)) {
       asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                    : "=r"(nb[0]), "=r"(nb[1]), "=r"(nb[2]), "=r"(nb[3]), "=r"(nb[4]), "=r"(nb[5]), "=r"(nb[6]),
                      "=r"(nb[7])
                    : "l"(g.nbr + 8 * b0));
     } else {
+      // every corner of a cell inside the brick is in the brick itself
 #pragma unroll
-      for (int c = 0; c < 8; c++) nb[c] = -1;
+      for (int c = 0; c < 8; c++) nb[c] = b0;
     }
-    const int cx = (i[0] & m) == m, cy = (i[1] & m) == m, cz = (i[2] & m) == m;
 #pragma unroll
     for (int c = 0; c < 8; c++) {
       const int dx = (c >> 2) & 1, dy = (c >> 1) & 1, dz = c & 1;
