@@ -38,7 +38,7 @@ BYTES_PER_RAY_RENDER = 12 + 4                          # rgb + count written
 # (one 1920x1080 frame of march_fwd_kernel<float, sparse, render>), from the ncu
 # capture summarised in profiles/march_fwd_render1080_sparse_f32.md; set to None
 # whenever that kernel changes until it is captured again.
-TRAFFIC_PER_LAUNCH = 53.457664e6 + 5.970432e6
+TRAFFIC_PER_LAUNCH = 53.413888e6 + 6.045184e6
 
 
 def _peaks():
