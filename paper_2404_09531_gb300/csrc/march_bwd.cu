@@ -2,12 +2,13 @@
 // recompute-in-backward march (sm_103a).
 //
 // Per bundle of 32 consecutive rays (one warp):
-//  1. each lane recomputes its ray's deferred MLP G(F, d) (Eq. 4) and the
-//     smoothness evaluations G(F, s_k) (Eqs. 9-10), forms dL/dC of the
-//     Charbonnier loss (Eq. 12) and backpropagates to dL/dF, dL/dT_N and the
-//     layer deltas.  The 32 rays' activations and deltas are staged in shared
-//     memory and the weight gradient, a sum over rays, is accumulated on
-//     tensor cores (mma.sync TF32, split operands) in registers;
+//  1. the warp recomputes the deferred MLP G(F, d) (Eq. 4) and the
+//     smoothness evaluations G(F, s_k) (Eqs. 9-10) of its 32 rays, forms
+//     dL/dC of the Charbonnier loss (Eq. 12) and backpropagates to dL/dF,
+//     dL/dT_N and the MLP weights; every MLP product is a warp-level
+//     tensor-core product over the 32 rays (mma.sync TF32 with split
+//     operands), the weight gradient accumulating in registers; in a fused
+//     training step it also adds the Charbonnier and smoothness loss terms;
 //  2. the warp re-marches every ray of the bundle exactly like the forward
 //     (same lattice windows, same product scan) for its saved sample count,
 //     and converts dL/dF into per-sample gradients:

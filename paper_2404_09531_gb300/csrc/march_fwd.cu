@@ -1,14 +1,21 @@
 // march_fwd.cu -- forward march: render and training forward (sm_103a).
 //
-// Persistent kernel, one warp per bundle of 32 rays (an 8x4 pixel tile for a
-// camera, 32 consecutive rays for a ray list), bundles taken from an atomic
-// work counter.  The warp marches the bundle's rays one after another with
-// its 32 lanes on 32 consecutive lattice samples of the ray (Sec. 4.1: only
-// samples inside the occupancy interval are evaluated; Eq. 1 compositing is a
-// lane-parallel product scan of 1 - M*alpha).  Consecutive samples of one ray
-// touch neighbouring texels, so one gather instruction of the warp hits few
-// cache lines.  After the bundle each lane shades its own ray with the
-// deferred MLP (Eq. 4).
+// Persistent kernel of 8 warps per CTA.  A CTA takes a super-tile of 8
+// bundles from an atomic work counter (16 x 16 pixels of a camera, or 256
+// consecutive rays of a ray list) so that its warps share L1 lines; a warp
+// owns a bundle of 32 rays (an 8 x 4 pixel tile).  The warp walks its rays
+// in order and packs their evaluated samples (Sec. 4.1: only samples inside
+// the occupancy interval are evaluated) into a 32-entry queue that may span
+// rays (packed.cuh); the 32 queued samples are gathered and activated in
+// parallel, composited with segmented lane scans (Eq. 1: a product scan of
+// 1 - M alpha per ray) and early termination is resolved per ray.  After
+// the bundle each lane shades its ray with the deferred MLP (Eq. 4): FP32 on
+// CUDA cores, or BF16 on tensor cores for a BF16 scene.
+//
+// Modes: render (pixels and sample counts); training forward with the loss
+// (per-ray state for the backward, MLP, Charbonnier and smoothness terms);
+// training forward without the loss (per-ray state only: the fused training
+// step lets the MLP backward, which evaluates the MLP anyway, add the loss).
 #include <cstdio>
 
 #include <type_traits>
