@@ -252,12 +252,24 @@ def test_scene_update_after_occupancy_change():
 
 
 def test_sync_is_bounded():
-    sc = synth.make_scene(1)
-    scene = gpu_scene(sc)
-    om.render(scene, camera=synth.make_cameras(1)[0])
-    om.sync(timeout_ms=60000)
+    """omerf_sync returns OMERF_ETIMEOUT while the stream is busy and OK once it
+    drains: eight 1920x1080 frames (~36 ms of GPU work) are queued, then a
+    zero-millisecond wait must give up, a long one must succeed."""
+    sc = synth.make_scene(2)
+    scene = gpu_scene(sc, table=oracle.brick_table(sc["spec"], sc["occ"]))
+    cams = synth.make_cameras(2)
+    om.render(scene, camera=cams[0], want_count=False)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for cam in cams:
+            om.render(scene, camera=cam, want_count=False, stream=stream)
     lib = om.lib()
-    assert lib.omerf_sync(None, 0) in (0, -5)  # an idle or busy stream: done or timed out, never blocks
+    handle = ctypes.c_void_p(stream.cuda_stream)
+    assert lib.omerf_sync(handle, 0) == -5
+    assert b"still busy" in lib.omerf_last_error()
+    assert lib.omerf_sync(handle, 60000) == 0
+    assert lib.omerf_sync(handle, 0) == 0
 
 
 def test_render_into_page_locked_host_memory():
@@ -284,3 +296,27 @@ def test_render_into_page_locked_host_memory():
                           ctypes.c_void_p(pageable.ctypes.data), None, None)
     assert rc == -3
     assert b"page-locked" in lib.omerf_last_error()
+
+
+def test_lattice_index_limit_and_long_rays():
+    """Rays with ~10^4 evaluated samples (n_max at its maximum, 65536, and at a
+    binding 4096), and a ray whose box crossing straddles lattice index 2^24,
+    where both sides stop at k = 2^24 - 1 (t_k = k step stays exact)."""
+    sc = synth.tiny_scene(seed=3)
+    step = 2.0 ** -16
+    rays = np.array([
+        [0.3, -0.2, 0.6, 0.0, 0.0, -1.0],       # ~20k lattice points in the box
+        [-0.5, 0.4, 0.6, 0.0, 0.0, -1.0],
+        [0.1, 0.1, 256.1, 0.0, 0.0, -1.0],      # k = 2^24 - 1 is reached at z = 0.1
+        [0.1, 0.1, 300.0, 0.0, 0.0, -1.0],      # the box lies beyond k = 2^24: nothing evaluated
+    ], np.float32)
+    for n_max in (65536, 4096):
+        osc = oracle.OracleScene(sc, step=step, n_max=n_max, t_thr=0.0)
+        ref = oracle.render(osc, rays)
+        assert ref["count"][0] > min(4096, n_max - 1) and ref["count"][3] == 0 and ref["count"][2] > 0
+        assert ref["k_last"][2] <= 2 ** 24 - 1
+        scene = gpu_scene(sc, step=step, n_max=n_max, t_thr=0.0)
+        rgb, cnt = _render_np(scene, rays=rays)
+        compare_render(rgb, cnt, ref, what=f"long rays n_max {n_max}")
+        if n_max == 4096:
+            assert cnt[0] == 4096 and cnt[1] == 4096
