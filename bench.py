@@ -266,7 +266,7 @@ def bench_precision_train(om, torch, dev, steps, warmup, flush, stream, n_rays=1
         torch.cuda.empty_cache()
         torch.cuda.reset_peak_memory_stats(dev)
         scene = om.scene_from_synth(sc, device=dev, feat_dtype=dt)
-        grads = om.binding._zero_grads(scene)
+        grads = om.zero_grads(scene)
         saved = torch.empty(n_rays * om.saved_bytes_per_ray() // 4, dtype=torch.float32, device=dev)
         for _ in range(warmup):
             om.train_step(scene, rays_d, tgt_d, dirs_d, lam=lam, grads=grads, saved=saved)
@@ -421,7 +421,7 @@ def run_native(args):
     target, _ = om.render(om.scene_from_synth(synth.perturb_scene(tsc), device=dev), rays=batch["rays"])
     rays_d = torch.as_tensor(batch["rays"]).to(dev)
     dirs_d = torch.as_tensor(batch["smooth_dirs"]).to(dev)
-    grads = om.binding._zero_grads(tscene)
+    grads = om.zero_grads(tscene)
     saved = torch.empty((1 << 18) * om.saved_bytes_per_ray() // 4, dtype=torch.float32, device=dev)
     lam = (1.0, 1e-2, 1e-4)
     for _ in range(args.warmup):
@@ -445,7 +445,7 @@ def run_native(args):
     # (with the paper's regulariser batches: 2^14 sparsity points, 2^10 entropy rays)
     pts_d = torch.as_tensor(synth.sparsity_points(tsc, 1 << 14)).to(dev)
     erays_d = torch.as_tensor(synth.entropy_rays(tsc, 1 << 10)).to(dev)
-    reg_grads = om.binding._zero_grads(tscene)
+    reg_grads = om.zero_grads(tscene)
     reg_loss = torch.zeros(1, dtype=torch.float32, device=dev)
     sp_ms, en_ms = [], []
     for it in range(args.warmup + args.steps):

@@ -394,10 +394,15 @@ def train_fwd(scene, rays, target, smooth_dirs=None, lam=(1.0, 1e-2, 0.0), strea
     return loss, saved, (rays_t, target_t, dirs_t, n, K)
 
 
-def _zero_grads(scene):
+def zero_grads(scene):
+    """Zeroed float32 gradient buffers shaped like the scene's parameters
+    (keys grid, p_xy, p_xz, p_yz, occ, mlp), as the training calls take them."""
     z = lambda t: torch.zeros(t.shape, dtype=torch.float32, device=t.device)  # noqa: E731
     return {"grid": z(scene.grid), "p_xy": z(scene.p_xy), "p_xz": z(scene.p_xz), "p_yz": z(scene.p_yz),
             "occ": z(scene.occ), "mlp": z(scene.mlp)}
+
+
+_zero_grads = zero_grads
 
 
 def train_bwd(scene, saved, inputs, lam=(1.0, 1e-2, 0.0), grad_scale=None, grads=None, stream=None):
@@ -405,9 +410,7 @@ def train_bwd(scene, saved, inputs, lam=(1.0, 1e-2, 0.0), grad_scale=None, grads
     rays_t, target_t, dirs_t, n, K = inputs
     if grads is None:
         grads = _zero_grads(scene)
-    gs = None
-    if grad_scale is not None:
-        gs = torch.as_tensor(grad_scale, dtype=torch.float32, device=scene.device).reshape(1).contiguous()
+    gs = _grad_scale(scene, grad_scale)
     _check(lib().omerf_train_bwd(scene.handle, _ptr(rays_t), _ptr(target_t), _ptr(dirs_t), n, K, _lam(lam),
                                  _ptr(saved), _ptr(gs), _ptr(grads["grid"]), _ptr(grads["p_xy"]),
                                  _ptr(grads["p_xz"]), _ptr(grads["p_yz"]), _ptr(grads["occ"]),

@@ -32,7 +32,7 @@ def _check(grads, ref, keys, what):
 
 
 def _sparsity(scene, osc, pts, lam=0.05):
-    grads = om.binding._zero_grads(scene)
+    grads = om.zero_grads(scene)
     loss = om.sparsity_loss(scene, pts, lam=lam, grads=grads)
     torch.cuda.synchronize()
     ref = oracle.sparsity(osc, pts, lam=lam)
@@ -40,7 +40,7 @@ def _sparsity(scene, osc, pts, lam=0.05):
 
 
 def _entropy(scene, osc, rays, lam=1e-3):
-    grads = om.binding._zero_grads(scene)
+    grads = om.zero_grads(scene)
     loss = om.entropy_loss(scene, rays, lam=lam, grads=grads)
     torch.cuda.synchronize()
     ref = oracle.entropy(osc, rays, lam=lam)
@@ -90,7 +90,7 @@ def test_sparsity_empty_accumulate_and_grad_scale():
     sc = synth.make_scene(3)
     scene = gpu_scene(sc)
     pts = synth.sparsity_points(sc, 3000, seed=4)
-    grads = om.binding._zero_grads(scene)
+    grads = om.zero_grads(scene)
     loss = torch.full((1,), 2.0, device="cuda")
     om.sparsity_loss(scene, np.zeros((0, 3), np.float32), grads=grads, loss=loss)
     torch.cuda.synchronize()
