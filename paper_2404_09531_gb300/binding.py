@@ -402,14 +402,12 @@ def zero_grads(scene):
             "occ": z(scene.occ), "mlp": z(scene.mlp)}
 
 
-_zero_grads = zero_grads
-
 
 def train_bwd(scene, saved, inputs, lam=(1.0, 1e-2, 0.0), grad_scale=None, grads=None, stream=None):
     """Training backward: accumulates grad_scale * dL/dparam into ``grads`` (float32)."""
     rays_t, target_t, dirs_t, n, K = inputs
     if grads is None:
-        grads = _zero_grads(scene)
+        grads = zero_grads(scene)
     gs = _grad_scale(scene, grad_scale)
     _check(lib().omerf_train_bwd(scene.handle, _ptr(rays_t), _ptr(target_t), _ptr(dirs_t), n, K, _lam(lam),
                                  _ptr(saved), _ptr(gs), _ptr(grads["grid"]), _ptr(grads["p_xy"]),
@@ -426,7 +424,7 @@ def train_step(scene, rays, target, smooth_dirs=None, lam=(1.0, 1e-2, 0.0), grad
         saved = torch.empty(max(n, 1) * saved_bytes_per_ray() // 4, dtype=torch.float32, device=scene.device)
     loss = torch.empty(4, dtype=torch.float32, device=scene.device)
     if grads is None:
-        grads = _zero_grads(scene)
+        grads = zero_grads(scene)
     _check(lib().omerf_train_step(scene.handle, _ptr(rays_t), _ptr(target_t), _ptr(dirs_t), n, K, _lam(lam),
                                   _ptr(saved), _ptr(loss), _ptr(grads["grid"]), _ptr(grads["p_xy"]),
                                   _ptr(grads["p_xz"]), _ptr(grads["p_yz"]), _ptr(grads["occ"]),
@@ -652,7 +650,7 @@ class Trainer:
         self.lam_sparsity, self.lam_entropy = lam_sparsity, lam_entropy
         self.betas, self.eps = betas, eps
         self.step_no = 0
-        self.grads = _zero_grads(scene)
+        self.grads = zero_grads(scene)
         self.master, self.shadow = {}, {}
         for k in ("grid", "p_xy", "p_xz", "p_yz", "occ", "mlp"):
             t = getattr(scene, k)
