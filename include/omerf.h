@@ -291,6 +291,12 @@ omerf_status omerf_extract_bricks(const int32_t grid_res[3], int32_t brick, cons
                                   const void *src, const int32_t *src_table, int32_t src_n_bricks,
                                   int32_t feat_dtype, void *pool, void *stream);
 
+/* 1 if the driver provides tensor-map encoding, so that omerf_extract_bricks
+ * copies bricks of up to 32 KB from a dense grid with tiled tensor-memory-
+ * accelerator loads (an (8, B, B, B) box of the grid per brick, zeros beyond
+ * its end) and bulk stores; 0 if it falls back to plain loads.  Host-only. */
+int32_t omerf_tma_available(void);
+
 /* Rows [k0, k1] of the XZ and YZ planes that any evaluated sample can read
  * (Sec. 4.4: the planes' z-resolution follows the occupancy plane's bounds).
  * Samples lie strictly inside (lo, hi), the hull of the non-empty cells;

@@ -77,6 +77,7 @@ SIGNATURES = {
     "omerf_entropy_loss": (ctypes.c_int, [_P, _P, _L, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P, _P]),
     "omerf_occupancy_grid": (ctypes.c_int, [_P, _P, _I, _P, _P, _P, _P]),
     "omerf_extract_bricks": (ctypes.c_int, [_P, _I, _P, _I, _P, _P, _I, _I, _P, _P]),
+    "omerf_tma_available": (ctypes.c_int32, []),
     "omerf_plane_crop_rows": (ctypes.c_int, [_P, _I, _P, _I, _P, _P, _P]),
     "omerf_crop_planes": (ctypes.c_int, [_P, _L, _I, _I, _I, _I, _P, _P]),
     "omerf_adam_step": (ctypes.c_int, [_P, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, _L, _P]),

@@ -13,6 +13,9 @@
 //                    reach, from the occupancy bounds              Sec. 4.4
 #include <cmath>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "internal.h"
 
 namespace omerf {
@@ -85,6 +88,71 @@ __global__ void __launch_bounds__(256) extract_bricks_kernel(int Lx, int Ly, int
       dst[e] = val;
     }
   }
+}
+
+// Bricks from a dense grid with the tensor memory accelerator: the grid is a
+// 4-D tensor (8 channels, z, y, x) whose (8, B, B, B) boxes are exactly the
+// pool's bricks ([B][B][B][8], x-major), so one tiled load brings a brick
+// into shared memory (vertices beyond the grid arrive as zeros) and one bulk
+// store writes it to its pool slot.  One thread per CTA drives the copies
+// through two buffers: the store of one brick overlaps the load of the
+// next.  Every wait on the load's mbarrier is bounded; a CTA that runs out
+// of tries stops.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__global__ void __launch_bounds__(32) extract_bricks_tma_kernel(const __grid_constant__ CUtensorMap src, int nbx,
+                                                               int nby, int nbz, int B,
+                                                               const int* __restrict__ table, int n_bricks,
+                                                               unsigned char* __restrict__ pool,
+                                                               unsigned brick_bytes) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  if (threadIdx.x != 0) return;
+  // tiled copies land on 128-byte aligned buffers (the launch adds the slack)
+  unsigned char* buf = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  const unsigned b0 = smem_addr(&bar[0]), b1 = smem_addr(&bar[1]);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0));
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b1));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  unsigned phase[2] = {0u, 0u};
+  int slot = 0;
+  const long long entries = (long long)nbx * nby * nbz;
+  for (long long t = blockIdx.x; t < entries; t += gridDim.x) {
+    const int b = __ldg(table + t);
+    if (b < 0 || b >= n_bricks) continue;
+    const int bk = (int)(t % nbz), bj = (int)((t / nbz) % nby), bi = (int)(t / ((long long)nbz * nby));
+    const unsigned bar_s = slot ? b1 : b0;
+    const unsigned dst = smem_addr(buf + (size_t)slot * brick_bytes);
+    // the bulk store that last read this buffer has finished reading it
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_s), "r"(brick_bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(&src), "r"(0), "r"(bk * B), "r"(bj * B), "r"(bi * B), "r"(bar_s)
+        : "memory");
+    bool done = false;
+    for (int tries = 0; tries < (1 << 20) && !done; tries++) {
+      unsigned ok;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(ok)
+          : "r"(bar_s), "r"(phase[slot])
+          : "memory");
+      done = ok != 0u;
+    }
+    if (!done) break;  // the load never completed: stop rather than wait forever
+    phase[slot] ^= 1u;
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(pool + (size_t)b * brick_bytes),
+                 "r"(dst), "r"(brick_bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    slot ^= 1;
+  }
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // Hull of the non-empty cells (z_min < z_max strictly: a sample needs
@@ -160,6 +228,24 @@ int grid_for(long long units, int threads, int cap_blocks) {
   return (int)g;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
 int sm_count() {
   int dev = 0, n = 0;
   cudaGetDevice(&dev);
@@ -209,6 +295,33 @@ omerf_status omerf_extract_bricks(const int32_t grid_res[3], int32_t brick, cons
   for (int a = 0; a < 3; a++) nb[a] = (grid_res[a] + brick - 1) / brick;
   const long long entries = (long long)nb[0] * nb[1] * nb[2];
   const int words = feat_dtype == OMERF_F32 ? 2 : 1;
+  const size_t esize = feat_dtype == OMERF_F32 ? 4 : 2;
+  const size_t brick_bytes = (size_t)brick * brick * brick * 8 * esize;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = src_table ? nullptr : tensor_map_encoder();
+  if (encode && brick_bytes <= 32768 && n_bricks > 0) {
+    // a dense source: tiled tensor-memory-accelerator copies
+    CUtensorMap map;
+    const cuuint64_t dims[4] = {8, (cuuint64_t)grid_res[2], (cuuint64_t)grid_res[1], (cuuint64_t)grid_res[0]};
+    const cuuint64_t strides[3] = {8 * esize, (cuuint64_t)grid_res[2] * 8 * esize,
+                                   (cuuint64_t)grid_res[1] * grid_res[2] * 8 * esize};
+    const cuuint32_t box[4] = {8, (cuuint32_t)brick, (cuuint32_t)brick, (cuuint32_t)brick};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(&map, feat_dtype == OMERF_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                             : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                              4, const_cast<void*>(src), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r == CUDA_SUCCESS) {
+      const size_t smem = 2 * brick_bytes + 128;
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(extract_bricks_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      const int blocks = grid_for(entries, 1, 6 * sm_count());
+      extract_bricks_tma_kernel<<<blocks, 32, smem, (cudaStream_t)stream>>>(
+          map, nb[0], nb[1], nb[2], brick, table, n_bricks, static_cast<unsigned char*>(pool), (unsigned)brick_bytes);
+      cudaError_t e = cudaGetLastError();
+      return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "brick extraction launch");
+    }
+  }
   const int blocks = grid_for(entries, 1, 16 * sm_count());
   extract_bricks_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(
       grid_res[0], grid_res[1], grid_res[2], brick, nb[0], nb[1], nb[2], table, n_bricks,
@@ -216,6 +329,8 @@ omerf_status omerf_extract_bricks(const int32_t grid_res[3], int32_t brick, cons
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "brick extraction launch");
 }
+
+int32_t omerf_tma_available(void) { return tensor_map_encoder() != nullptr ? 1 : 0; }
 
 omerf_status omerf_plane_crop_rows(const float plane_z[2], int32_t Rz, const float* occ, int32_t M, int32_t* rows,
                                    float* z_range, void* stream) {

@@ -77,6 +77,21 @@ def test_extract_bricks_from_dense_and_from_older_pool(dtype):
     np.testing.assert_array_equal(p2.float().cpu().numpy(), r2)
 
 
+def test_dense_extraction_uses_the_tensor_memory_accelerator():
+    """Bricks from a dense grid are copied by tiled TMA loads (the driver
+    provides tensor-map encoding, so that path is taken), bit-exactly,
+    including a brick that overhangs the grid on every axis (zeros beyond)."""
+    spec = dataclasses.replace(synth.scene_spec(1), brick=8, L=(21, 19, 13))
+    sc = synth.make_scene(1)
+    dense = np.random.default_rng(9).normal(0, 1, (*spec.L, 8)).astype(np.float32)
+    table = oracle.brick_table(spec, sc["occ"])
+    table_d, dense_d = torch.as_tensor(table).cuda(), torch.as_tensor(dense).cuda()
+    assert om.lib().omerf_tma_available() == 1
+    pool = om.extract_bricks(spec.L, 8, table_d, dense_d)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(pool.cpu().numpy(), oracle.extract_bricks(spec.L, 8, table, dense))
+
+
 def test_extracted_pool_renders_like_the_dense_grid():
     """Table built on the GPU from the occupancy plane, pool extracted on the
     GPU from the dense grid: the brick scene renders like the dense scene."""
