@@ -35,10 +35,11 @@ import synth  # noqa: E402
 BYTES_PER_SAMPLE = {"f32": 640 + 8, "bf16": 320 + 8}  # feature gather + occupancy bounds
 BYTES_PER_RAY_RENDER = 12 + 4                          # rgb + count written
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel
-# (one 1920x1080 frame of march_fwd_kernel<float, sparse, render>), from the ncu
-# capture summarised in profiles/march_fwd_render1080_sparse_f32.md; set to None
-# whenever that kernel changes until it is captured again.
-TRAFFIC_PER_LAUNCH = 53.413888e6 + 6.045184e6
+# (one launch of march_fwd_kernel<float, sparse, render> over the step's eight
+# 1920x1080 cameras), from the ncu capture summarised in
+# profiles/march_fwd_render1080x8_sparse_f32.md; set to None whenever that
+# kernel changes until it is captured again.
+TRAFFIC_PER_LAUNCH = 172457984.0 + 175561216.0
 
 
 def _peaks():
@@ -207,19 +208,19 @@ def cpu_baseline_sample(sc, cams, budget_s=12.0):
 # secondary workloads reported in the same line: BF16 vs FP32
 # ---------------------------------------------------------------------------
 def _time_renders(om, torch, scene, cams, steps, warmup, flush, stream):
+    n = sum(c["width"] * c["height"] for c in cams)
+    out = torch.empty((n, 3), dtype=torch.float32, device=scene.device)
     for _ in range(warmup):
-        for cam in cams:
-            om.render(scene, camera=cam, want_count=False)
+        om.render_cameras(scene, cams, out=out, want_count=False)
     ms = []
     for _ in range(steps):
         flush.fill_(1.0)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in cams]
-        for (a, b), cam in zip(ev, cams):
-            a.record(stream)
-            om.render(scene, camera=cam, want_count=False)
-            b.record(stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        om.render_cameras(scene, cams, out=out, want_count=False)
+        b.record(stream)
         torch.cuda.synchronize()
-        ms.append(sum(a.elapsed_time(b) for a, b in ev))
+        ms.append(a.elapsed_time(b))
     return float(np.mean(ms))
 
 
@@ -363,15 +364,17 @@ def run_native(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    rays_per_step = sum(c["width"] * c["height"] for c in cams)
+    dev_rgb = torch.empty((rays_per_step, 3), dtype=torch.float32, device=dev)
+
     def step(events=None):
-        outs = []
-        for i, cam in enumerate(cams):
-            if events is not None:
-                events[i][0].record(stream)
-            outs.append(om.render(scene, camera=cam, want_count=False))
-            if events is not None:
-                events[i][1].record(stream)
-        return outs
+        # the step's cameras in one persistent launch
+        if events is not None:
+            events[0][0].record(stream)
+        om.render_cameras(scene, cams, out=dev_rgb, want_count=False)
+        if events is not None:
+            events[0][1].record(stream)
+        return dev_rgb
 
     for _ in range(args.warmup):
         step()
@@ -381,7 +384,6 @@ def run_native(args):
     for cam in cams:
         _, c = om.render(scene, camera=cam)
         samples_per_step += int(c.sum().item())
-    rays_per_step = sum(c["width"] * c["height"] for c in cams)
 
     clocks = ClockSampler(None)
     if ws > 1:
@@ -393,7 +395,7 @@ def run_native(args):
     step_ms = []
     for _ in range(args.steps):
         flush.fill_(1.0)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in cams]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))]
         step(ev)
         torch.cuda.synchronize()
         ms = [a.elapsed_time(b) for a, b in ev]
@@ -408,21 +410,20 @@ def run_native(args):
     value = ws * rays_per_step / (t_step * 1e-3) / 1e6
 
     # ---- end to end through the public API, host buffers ----
-    host_rgb = [torch.empty((c["width"] * c["height"], 3), dtype=torch.float32, pin_memory=True) for c in cams]
+    host_rgb = torch.empty((rays_per_step, 3), dtype=torch.float32, pin_memory=True)
     e2e_ms = []
     for i in range(args.warmup + args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for cam, h in zip(cams, host_rgb):
-            om.render(scene, camera=cam, out=h, want_count=False)
+        om.render_cameras(scene, cams, out=host_rgb, want_count=False)
         b.record(stream)
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
     e2e_step = float(np.mean(e2e_ms))
-    d2h = sum(h.numel() * 4 for h in host_rgb)
+    d2h = host_rgb.numel() * 4
     h2d = 64 * len(cams)  # camera structs (the step's only input)
 
     # ---- training step (config 3) ----
@@ -505,7 +506,7 @@ def run_native(args):
 
     hbm, peak_kind = _peaks()
     t_launch = float(np.mean(per_launch)) * 1e-3
-    bytes_launch = (samples_per_step * BYTES_PER_SAMPLE["f32"] + rays_per_step * BYTES_PER_RAY_RENDER) / len(cams)
+    bytes_launch = samples_per_step * BYTES_PER_SAMPLE["f32"] + rays_per_step * BYTES_PER_RAY_RENDER
     achieved = bytes_launch / t_launch / 1e9
     cfg = _workload_config()
     cfg["samples_per_step"] = samples_per_step
@@ -541,7 +542,7 @@ def run_native(args):
                            "achieved_gbs": 28.0 * n_params / (t_adam * 1e-3) / 1e9,
                            "note": "28 B per parameter (read p, g, m, v; write p, m, v)"}},
         "extraction": extraction,
-        "gpu_launches": args.steps * len(cams),
+        "gpu_launches": args.steps,
         "clocks": clk,
     }
     if precision is not None:

@@ -190,6 +190,16 @@ omerf_status omerf_render(const omerf_scene *scene, const omerf_camera *cam, con
 omerf_status omerf_render_noalloc(const omerf_scene_desc *desc, const omerf_camera *cam, const float *rays,
                                   int64_t n, float *rgb, int32_t *count, void *stream);
 
+/* Render several cameras in one launch (a step of a multi-view frame set):
+ * rgb [sum of width * height][3] and count in camera order, memory as for
+ * omerf_render.  The cameras' super-tiles share one persistent launch (up to
+ * 16 cameras per launch; more are rendered in groups of 16), so no SM idles
+ * at the end of one frame while the next waits.  The camera records are
+ * copied to the scene's device state on `stream`, which therefore orders
+ * this call with the scene's other calls as usual. */
+omerf_status omerf_render_cameras(const omerf_scene *scene, const omerf_camera *cams, int32_t n_cams,
+                                  float *rgb, int32_t *count, void *stream);
+
 /* Bytes of per-ray state that omerf_train_fwd writes for omerf_train_bwd. */
 int64_t omerf_saved_bytes_per_ray(void);
 

@@ -69,6 +69,7 @@ SIGNATURES = {
     "omerf_ray_interval": (ctypes.c_int, [_P, _P, _P, _L, _P, _P]),
     "omerf_render": (ctypes.c_int, [_P, _P, _P, _L, _P, _P, _P]),
     "omerf_render_noalloc": (ctypes.c_int, [_P, _P, _P, _L, _P, _P, _P]),
+    "omerf_render_cameras": (ctypes.c_int, [_P, _P, _I, _P, _P, _P]),
     "omerf_saved_bytes_per_ray": (ctypes.c_int64, []),
     "omerf_train_fwd": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P]),
     "omerf_train_bwd": (ctypes.c_int, [_P, _P, _P, _P, _L, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -317,6 +318,27 @@ def render(scene: Scene, camera=None, rays=None, out=None, count_out=None, strea
         if count_out is not None:
             count_out.copy_(count, non_blocking=True)
         return out, count_out
+    return rgb, count
+
+
+def render_cameras(scene: Scene, cameras, out=None, count_out=None, stream=None, want_count=True):
+    """Render several cameras in one launch: (rgb [sum n, 3], count [sum n])
+    in camera order.  ``out`` / ``count_out`` may be device tensors or
+    page-locked CPU tensors, which the kernel writes directly."""
+    cams = list(cameras)
+    arr = (_Camera * max(len(cams), 1))(*[camera_struct(c) for c in cams])
+    n = sum(int(c["width"]) * int(c["height"]) for c in cams)
+    dev = scene.device
+    rgb = out if out is not None else torch.empty((n, 3), dtype=torch.float32, device=dev)
+    count = count_out if count_out is not None else (
+        torch.empty(n, dtype=torch.int32, device=dev) if want_count else None)
+    for t, name in ((rgb, "out"), (count, "count_out")):
+        if t is not None and (not t.is_contiguous() or (not t.is_cuda and not t.is_pinned())):
+            raise OmerfError(f"{name} must be a contiguous device tensor or page-locked CPU tensor")
+    if rgb.numel() != 3 * n or (count is not None and count.numel() != n):
+        raise OmerfError("output sizes do not match the cameras")
+    _check(lib().omerf_render_cameras(scene.handle, arr, len(cams), _ptr(rgb), _ptr(count), _stream(stream)),
+           "omerf_render_cameras")
     return rgb, count
 
 

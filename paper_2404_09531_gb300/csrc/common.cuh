@@ -58,6 +58,15 @@ struct Cam {
   int width, height;
 };
 
+// One camera of a multi-camera render: its first super-tile and first ray
+// in the launch's numbering, and its super-tiles per row.
+struct CamRec {
+  Cam cam;
+  long long super_start, ray_start;
+  int super_x, pad;
+};
+constexpr int kMaxCams = 16;  // cameras per multi-camera launch
+
 // ---------------------------------------------------------------------------
 // rays
 // ---------------------------------------------------------------------------

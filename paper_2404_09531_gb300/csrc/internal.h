@@ -13,6 +13,7 @@ struct omerf_scene {
   unsigned* counters = nullptr;    // device: per-launch work counters
   float2* chull = nullptr;         // device: coarse max-pooled occupancy grid [Mc][Mc]
   int* nbr = nullptr;              // device: brick neighbour records [n_bricks][8] (brick grids)
+  omerf::CamRec* cams = nullptr;   // device: camera records of a multi-camera render [kMaxCams]
   int clog2 = 0, Mc = 1;
   mutable std::atomic<unsigned> seq{0};
   int device = 0;
@@ -37,6 +38,9 @@ cudaError_t launch_march_bwd(const omerf_scene* s, const float* rays, const floa
                              long n, int K, const float lam[3], float* saved, const float* grad_scale,
                              float* g_grid, float* g_xy, float* g_xz, float* g_yz, float* g_occ,
                              float* g_mlp, float* loss, cudaStream_t stream);
+
+cudaError_t launch_march_fwd_cams(const omerf_scene* s, const CamRec* cams, int n_cams, long n_super, long n,
+                                  float* rgb, int* count, cudaStream_t stream);
 
 int persistent_blocks(const void* kernel, int threads, size_t smem, int num_sms);
 

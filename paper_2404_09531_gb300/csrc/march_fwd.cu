@@ -133,6 +133,10 @@ struct FwdArgs {
   float* saved;
   float* loss;
   unsigned* counter;
+  // multi-camera render (n_cams > 0): device camera records, super-tiles in
+  // camera order
+  const CamRec* cams;
+  int n_cams;
 };
 
 #ifndef OMERF_FWD_MINB
@@ -175,7 +179,18 @@ __global__ void __launch_bounds__(kThreads, OMERF_FWD_MINB) march_fwd_kernel(con
     long rid;
     bool valid;
     float o[3] = {0.0f, 0.0f, 0.0f}, d[3] = {0.0f, 0.0f, 1.0f};
-    if (a.use_cam) {
+    if (a.n_cams > 0) {
+      int c = 0;
+      while (c + 1 < a.n_cams && (long long)sb >= a.cams[c + 1].super_start) c++;
+      const CamRec& cr = a.cams[c];
+      const unsigned lsb = (unsigned)((long long)sb - cr.super_start);
+      const int sx = (int)(lsb % (unsigned)cr.super_x), sy = (int)(lsb / (unsigned)cr.super_x);
+      const int tx = 2 * sx + (warp & 1), ty = 4 * sy + (warp >> 1);
+      const int px = tx * 8 + (lane & 7), py = ty * 4 + (lane >> 3);
+      valid = px < cr.cam.width && py < cr.cam.height;
+      rid = (long)cr.ray_start + (long)py * cr.cam.width + px;
+      if (valid) camera_ray(cr.cam, px, py, o, d);
+    } else if (a.use_cam) {
       const int sx = (int)(sb % (unsigned)a.super_x), sy = (int)(sb / (unsigned)a.super_x);
       const int tx = 2 * sx + (warp & 1), ty = 4 * sy + (warp >> 1);
       const int px = tx * 8 + (lane & 7), py = ty * 4 + (lane >> 3);
@@ -347,6 +362,26 @@ cudaError_t launch_march_fwd(const omerf_scene* s, const Cam* cam, const float* 
     return sparse ? launch_variant<float, true, true, false>(s, a, stream)
                   : launch_variant<float, false, true, false>(s, a, stream);
   }
+  if (bf16) return sparse ? launch_variant<__nv_bfloat16, true, false>(s, a, stream)
+                          : launch_variant<__nv_bfloat16, false, false>(s, a, stream);
+  return sparse ? launch_variant<float, true, false>(s, a, stream) : launch_variant<float, false, false>(s, a, stream);
+}
+
+
+cudaError_t launch_march_fwd_cams(const omerf_scene* s, const CamRec* cams, int n_cams, long n_super, long n,
+                                  float* rgb, int* count, cudaStream_t stream) {
+  FwdArgs a{};
+  a.use_cam = 1;
+  a.cams = cams;
+  a.n_cams = n_cams;
+  a.n_super = n_super;
+  a.n = n;
+  a.rgb = rgb;
+  a.count = count;
+  if (a.n_super == 0) return cudaSuccess;
+  a.counter = next_counter(s, stream);
+  const bool bf16 = s->desc.feat_dtype == OMERF_BF16;
+  const bool sparse = s->desc.brick > 0;
   if (bf16) return sparse ? launch_variant<__nv_bfloat16, true, false>(s, a, stream)
                           : launch_variant<__nv_bfloat16, false, false>(s, a, stream);
   return sparse ? launch_variant<float, true, false>(s, a, stream) : launch_variant<float, false, false>(s, a, stream);

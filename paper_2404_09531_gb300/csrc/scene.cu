@@ -425,6 +425,7 @@ omerf_status omerf_scene_create(const omerf_scene_desc* desc, void* stream, omer
   if (e != cudaSuccess) { cudaGetLastError(); cudaFree(s->state); delete s; set_error("cudaMalloc: %s", cudaGetErrorString(e)); return OMERF_ENOMEM; }
   choose_coarse_level(s);
   e = cudaMalloc(&s->chull, (size_t)s->Mc * s->Mc * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&s->cams, kMaxCams * sizeof(CamRec));
   if (e == cudaSuccess && desc->brick && desc->n_bricks > 0)
     e = cudaMalloc(&s->nbr, (size_t)desc->n_bricks * 8 * sizeof(int));
   if (e != cudaSuccess) {
@@ -485,6 +486,7 @@ void omerf_scene_destroy(omerf_scene* s) {
   cudaFree(s->counters);
   cudaFree(s->chull);
   cudaFree(s->nbr);
+  cudaFree(s->cams);
   delete s;
 }
 
@@ -582,6 +584,45 @@ omerf_status omerf_render(const omerf_scene* s, const omerf_camera* cam, const f
   cudaError_t e = launch_march_fwd(s, cam ? &k : nullptr, rays, n, rgb, count, nullptr, nullptr, 0, nullptr,
                                    nullptr, nullptr, (cudaStream_t)stream);
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "render launch");
+}
+
+omerf_status omerf_render_cameras(const omerf_scene* s, const omerf_camera* cams, int32_t n_cams, float* rgb,
+                                  int32_t* count, void* stream) {
+  if (!s || (!cams && n_cams > 0)) { set_error("NULL argument"); return OMERF_EINVAL; }
+  if (n_cams < 0) { set_error("n_cams must be >= 0"); return OMERF_ESHAPE; }
+  if (n_cams == 0) return OMERF_OK;
+  if (!rgb) { set_error("rgb is NULL"); return OMERF_EINVAL; }
+  omerf_status st;
+  for (int c = 0; c < n_cams; c++)
+    if ((st = validate_camera(&cams[c], (int64_t)cams[c].width * cams[c].height)) != OMERF_OK) return st;
+  void *rd = nullptr, *cd = nullptr;
+  if ((st = output_ptr(rgb, &rd, "rgb")) != OMERF_OK) return st;
+  if ((st = output_ptr(count, &cd, "count")) != OMERF_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  long ray0 = 0;
+  for (int c0 = 0; c0 < n_cams; c0 += kMaxCams) {
+    const int m = std::min(kMaxCams, n_cams - c0);
+    CamRec rec[kMaxCams];
+    long supers = 0, rays = 0;
+    for (int c = 0; c < m; c++) {
+      const omerf_camera& k = cams[c0 + c];
+      rec[c].cam = to_cam(&k);
+      rec[c].super_x = (k.width + 15) / 16;
+      rec[c].super_start = supers;
+      rec[c].ray_start = rays;
+      rec[c].pad = 0;
+      supers += (long)rec[c].super_x * ((k.height + 15) / 16);
+      rays += (long)k.width * k.height;
+    }
+    // pageable source: the copy is staged before the call returns
+    cudaError_t e = cudaMemcpyAsync(s->cams, rec, m * sizeof(CamRec), cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "camera upload");
+    e = launch_march_fwd_cams(s, s->cams, m, supers, rays, static_cast<float*>(rd) + 3 * ray0,
+                              cd ? static_cast<int32_t*>(cd) + ray0 : nullptr, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "render launch");
+    ray0 += rays;
+  }
+  return OMERF_OK;
 }
 
 int64_t omerf_saved_bytes_per_ray(void) { return (int64_t)kSavedFloats * sizeof(float); }

@@ -320,3 +320,29 @@ def test_lattice_index_limit_and_long_rays():
         compare_render(rgb, cnt, ref, what=f"long rays n_max {n_max}")
         if n_max == 4096:
             assert cnt[0] == 4096 and cnt[1] == 4096
+
+
+def test_render_cameras_in_one_launch():
+    """Several cameras of different sizes rendered in one launch equal their
+    single-camera renders, in camera order, into device or page-locked host
+    buffers; more than 16 cameras are rendered in groups."""
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    cams = synth.make_cameras(3, n=3)
+    small = dict(cams[2], width=37, height=23, cx=np.float32(18.5), cy=np.float32(11.5))
+    cams = [cams[0], small, synth.make_cameras(1)[0], cams[1]]
+    rgb, cnt = om.render_cameras(scene, cams)
+    torch.cuda.synchronize()
+    parts = [om.render(scene, camera=c) for c in cams]
+    torch.cuda.synchronize()
+    assert torch.equal(rgb, torch.cat([p[0] for p in parts])) and torch.equal(cnt, torch.cat([p[1] for p in parts]))
+    n = rgb.shape[0]
+    h_rgb = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    om.render_cameras(scene, cams, out=h_rgb, want_count=False)
+    torch.cuda.synchronize()
+    assert torch.equal(h_rgb, rgb.cpu())
+    many = [cams[1]] * 17 + [cams[0]]
+    rgb17, _ = om.render_cameras(scene, many)
+    torch.cuda.synchronize()
+    ref17 = torch.cat([parts[1][0]] * 17 + [parts[0][0]])
+    assert torch.equal(rgb17, ref17)
