@@ -523,9 +523,9 @@ def run_native(args):
                      "kernel": "march_fwd_kernel<float, sparse, render>",
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "algorithmic_bytes_per_launch": bytes_launch,
-                     "note": "the 648 B/sample feature gather is served from L1 (85 % hits) and L2 (96 %); "
+                     "note": "the 648 B/sample feature gather is served from L1 (85-88 % hits) and L2 (97 %); "
                              "DRAM moves only the frame's working set (traffic), so frac exceeds 1; the "
-                             "binding unit is the L1 data pipe, 83 % busy under ncu"},
+                             "binding unit is the L1 data pipe, 77-83 % busy under ncu"},
         "e2e": {"value": ws * rays_per_step / (e2e_step * 1e-3) / 1e6, "unit": "Mrays/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "train": {"metric": "Mrays/s fwd+bwd train", "value": (1 << 18) / (t_train * 1e-3) / 1e6,
