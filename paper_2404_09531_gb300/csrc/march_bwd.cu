@@ -796,11 +796,15 @@ __global__ void __launch_bounds__(kThreads, OMERF_BWD_MINB) march_bwd_kernel(con
 template <class FT, bool SPARSE>
 static cudaError_t launch_bwd_variant(const omerf_scene* s, const BwdArgs& a, cudaStream_t stream) {
   auto kern = march_bwd_kernel<FT, SPARSE>;
-  static int blocks[64] = {0};
+  static std::atomic<int> blocks[64];  // per device: resident CTAs of this variant
   const int dev = s->device & 63;
-  if (blocks[dev] == 0) blocks[dev] = persistent_blocks((const void*)kern, kThreads, 0, s->num_sms);
+  int nb = blocks[dev].load(std::memory_order_relaxed);
+  if (nb == 0) {
+    nb = persistent_blocks((const void*)kern, kThreads, 0, s->num_sms);
+    blocks[dev].store(nb, std::memory_order_relaxed);
+  }
   long want = (a.n_bundles + (kThreads / 32) - 1) / (kThreads / 32);
-  int grid = (int)(want < blocks[dev] ? want : blocks[dev]);
+  int grid = (int)(want < nb ? want : nb);
   if (grid < 1) grid = 1;
   kern<<<grid, kThreads, 0, stream>>>(s->geo, a);
   return cudaGetLastError();
@@ -808,14 +812,16 @@ static cudaError_t launch_bwd_variant(const omerf_scene* s, const BwdArgs& a, cu
 
 static cudaError_t launch_mlp_bwd(const omerf_scene* s, const BwdArgs& a, cudaStream_t stream) {
   const size_t smem = sizeof(MlpBwdShared) + (size_t)(kBwdThreads / 32) * 32 * kRow * sizeof(float);
-  static int blocks[64] = {0};
+  static std::atomic<int> blocks[64];  // per device: resident CTAs
   const int dev = s->device & 63;
-  if (blocks[dev] == 0) {
+  int nb = blocks[dev].load(std::memory_order_relaxed);
+  if (nb == 0) {
     cudaFuncSetAttribute((const void*)mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    blocks[dev] = persistent_blocks((const void*)mlp_bwd_kernel, kBwdThreads, smem, s->num_sms);
+    nb = persistent_blocks((const void*)mlp_bwd_kernel, kBwdThreads, smem, s->num_sms);
+    blocks[dev].store(nb, std::memory_order_relaxed);
   }
   long want = (a.n_bundles + (kBwdThreads / 32) - 1) / (kBwdThreads / 32);
-  int grid = (int)(want < blocks[dev] ? want : blocks[dev]);
+  int grid = (int)(want < nb ? want : nb);
   if (grid < 1) grid = 1;
   mlp_bwd_kernel<<<grid, kBwdThreads, smem, stream>>>(s->geo, a);
   return cudaGetLastError();

@@ -310,11 +310,15 @@ int persistent_blocks(const void* kernel, int threads, size_t smem, int num_sms)
 template <class FT, bool SPARSE, bool TRAIN, bool LOSS = TRAIN>
 static cudaError_t launch_variant(const omerf_scene* s, const FwdArgs& a, cudaStream_t stream) {
   auto kern = march_fwd_kernel<FT, SPARSE, TRAIN, LOSS>;
-  static int blocks[64] = {0};
+  static std::atomic<int> blocks[64];  // per device: resident CTAs of this variant
   const int dev = s->device & 63;
-  if (blocks[dev] == 0) blocks[dev] = persistent_blocks((const void*)kern, kThreads, 0, s->num_sms);
+  int nb = blocks[dev].load(std::memory_order_relaxed);
+  if (nb == 0) {
+    nb = persistent_blocks((const void*)kern, kThreads, 0, s->num_sms);
+    blocks[dev].store(nb, std::memory_order_relaxed);
+  }
   long want = a.n_super;
-  int grid = (int)(want < blocks[dev] ? want : blocks[dev]);
+  int grid = (int)(want < nb ? want : nb);
   if (grid < 1) grid = 1;
   kern<<<grid, kThreads, 0, stream>>>(s->geo, a);
   return cudaGetLastError();

@@ -229,17 +229,17 @@ omerf_status check_reg_args(const omerf_scene* s, const void* in, int64_t n, flo
 
 template <class K>
 int reg_grid(K kern, long units_per_block, long n, int num_sms) {
-  static int per_sm[64] = {0};
+  static std::atomic<int> per_sm[64];  // per device: resident CTAs of this kernel
   int dev = 0;
   cudaGetDevice(&dev);
   dev &= 63;
-  if (per_sm[dev] == 0) {
-    int b = 0;
+  int b = per_sm[dev].load(std::memory_order_relaxed);
+  if (b == 0) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, 0) != cudaSuccess || b < 1) b = 1;
-    per_sm[dev] = b;
+    per_sm[dev].store(b, std::memory_order_relaxed);
   }
   const long want = (n + units_per_block - 1) / units_per_block;
-  const long cap = (long)per_sm[dev] * num_sms;
+  const long cap = (long)b * num_sms;
   return (int)std::max(1L, std::min(want, cap));
 }
 
