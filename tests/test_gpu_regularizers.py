@@ -173,3 +173,22 @@ def test_entropy_without_gradients_and_empty():
     empty = om.entropy_loss(scene, np.zeros((0, 6), np.float32))
     torch.cuda.synchronize()
     assert empty.item() == 0.0
+
+
+def test_regularisers_bf16_brick_grid():
+    """Both regularisers on a BF16 brick pool (the sparse BF16 kernel variants)
+    against the oracle on the rounded pool and planes."""
+    sc = synth.make_scene(1)
+    spec = dataclasses.replace(sc["spec"], brick=8)
+    table = oracle.brick_table(spec, sc["occ"])
+    rb = lambda a: torch.as_tensor(a).to(torch.bfloat16).float().numpy()  # noqa: E731
+    pool = rb(oracle.extract_bricks(spec.L, 8, table, sc["grid"]))
+    sb = dict(sc, spec=spec, grid=pool, table=table, p_xy=rb(sc["p_xy"]), p_xz=rb(sc["p_xz"]), p_yz=rb(sc["p_yz"]))
+    scene = gpu_scene(sb, feat_dtype=torch.bfloat16)
+    osc = oracle.OracleScene(sb)
+    loss, grads, ref = _sparsity(scene, osc, synth.sparsity_points(sc, 4096))
+    assert loss == pytest.approx(ref["loss"], rel=1e-5)
+    _check(grads, ref, FEAT, "sparsity bf16 bricks")
+    loss, grads, ref = _entropy(scene, osc, synth.entropy_rays(sc, 512))
+    assert loss == pytest.approx(ref["loss"], rel=1e-4)
+    _check(grads, ref, FEAT + ("occ",), "entropy bf16 bricks")

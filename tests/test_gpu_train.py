@@ -220,3 +220,24 @@ def test_config5_full_batch_bf16_as_benchmarked():
     ref = oracle.train(oracle.OracleScene(sc_b), batch["rays"], batch["target"], batch["smooth_dirs"], lam=LAM)
     np.testing.assert_allclose(float(res["loss"][0]), ref["loss"], rtol=1e-5)
     _check_grads(res, ref, what="config 5 full bf16")
+
+
+def test_bf16_brick_grid_gradients():
+    """BF16 features in a brick pool (the sparse BF16 forward and re-march
+    variants) against the oracle on the BF16-rounded pool and planes."""
+    sc = synth.tiny_scene(seed=7, n_rays=256, L=(10, 9, 8))
+    B = 4
+    spec = dataclasses.replace(sc["spec"], brick=B)
+    table = oracle.brick_table(spec, sc["occ"])
+    rb = lambda a: torch.as_tensor(a).to(torch.bfloat16).float().numpy()  # noqa: E731
+    pool = rb(oracle.extract_bricks(spec.L, B, table, sc["grid"]))
+    sb = dict(sc, spec=spec, grid=pool, table=table, p_xy=rb(sc["p_xy"]), p_xz=rb(sc["p_xz"]), p_yz=rb(sc["p_yz"]))
+    batch = {k: sc[k] for k in ("rays", "target", "smooth_dirs")}
+    scene = gpu_scene(sb, feat_dtype=torch.bfloat16)
+    assert scene.feat_dtype == torch.bfloat16 and scene.brick == B
+    res = om.train_step(scene, batch["rays"], batch["target"], batch["smooth_dirs"], lam=(1.0, 0.1, 0.01))
+    torch.cuda.synchronize()
+    ref = oracle.train(oracle.OracleScene(sb), batch["rays"], batch["target"], batch["smooth_dirs"],
+                       lam=(1.0, 0.1, 0.01))
+    np.testing.assert_allclose(float(res["loss"][0]), ref["loss"], rtol=1e-5)
+    _check_grads(res, ref, what="bf16 brick")
