@@ -11,6 +11,7 @@ Functions follow Oblique-MERF (arXiv 2404.09531):
   brick_table                                                  Sec. 4.4 brick allocation
   sparsity / entropy (loss + analytic gradient)                Eqs. 13, 14 (Sec. 4.3)
   occupancy_grid / extract_bricks / plane_crop_rows            Sec. 4.4, Sec. 5.3 extraction
+  working_set                                                  parameters a render reads (Sec. 4.4 viewer)
 
 Parity status: every function is pinned in tests/test_oracle*.py by closed
 forms, invariants, library routines or brute force (see that file).  No
@@ -101,6 +102,8 @@ def _load():
         lib.or_plane_crop_rows.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, P]
         lib.or_entropy.restype = ctypes.c_double
         lib.or_entropy.argtypes = [P, P, ctypes.c_long, ctypes.c_double, ctypes.c_double, P, P, P, P, P]
+        lib.or_working_set.restype = ctypes.c_long
+        lib.or_working_set.argtypes = [P, P, ctypes.c_long, P, P, P, P, P, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -177,6 +180,27 @@ def render(oscene: OracleScene, rays: np.ndarray, nthreads: int = 0) -> dict:
                        _ptr(out["F"]), _ptr(out["TN"]), _ptr(out["ambiguous"]),
                        _ptr(out["k_first"]), _ptr(out["k_last"]), int(nthreads))
     out["unalloc"] = int(ua)
+    return out
+
+
+def working_set(oscene: OracleScene, rays: np.ndarray, nthreads: int = 0) -> dict:
+    """Which parameters a render of the rays reads at least once: boolean masks
+    over the grid vertices (dense [Lx, Ly, Lz] or pool [nb, B, B, B]), the
+    texels of each plane and the occupancy cells, plus the evaluated-sample
+    count.  A vertex or texel is read by every evaluated sample whose
+    interpolation stencil holds it (all 8 grid corners, 4 texels per plane,
+    whatever their weight); an occupancy cell by every in-box lattice sample
+    the march tests before the ray stops."""
+    lib = _load()
+    rays = np.ascontiguousarray(rays, np.float32)
+    m = {"grid": np.zeros(oscene.grid.shape[:-1], np.uint8), "p_xy": np.zeros(oscene.pxy.shape[:-1], np.uint8),
+         "p_xz": np.zeros(oscene.pxz.shape[:-1], np.uint8), "p_yz": np.zeros(oscene.pyz.shape[:-1], np.uint8),
+         "occ": np.zeros(oscene.occ.shape[:-1], np.uint8)}
+    d = oscene.desc()
+    samples = lib.or_working_set(ctypes.byref(d), _ptr(rays), rays.shape[0], _ptr(m["grid"]), _ptr(m["p_xy"]),
+                                 _ptr(m["p_xz"]), _ptr(m["p_yz"]), _ptr(m["occ"]), int(nthreads))
+    out = {k: v.astype(bool) for k, v in m.items()}
+    out["samples"] = int(samples)
     return out
 
 

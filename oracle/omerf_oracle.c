@@ -942,3 +942,65 @@ int or_plane_crop_rows(const float *aabb, int Rz, const float *occ, int M, int32
     return 0;
 }
 
+
+/* ------------------------------------------------------------------ */
+/* working set of a render (Sec. 4.4 viewer)                           */
+/* ------------------------------------------------------------------ */
+static void mark(uint8_t *m, long i)
+{
+    __atomic_store_n(&m[i], (uint8_t)1, __ATOMIC_RELAXED);
+}
+
+/* Marks every parameter a render of the rays reads at least once: the 8 grid
+ * vertices (dense index or pool slot, over [vertices] = [Lx Ly Lz] or
+ * [nb B^3]) and the 4 texels of each plane of every evaluated sample, and
+ * the occupancy cell of every lattice sample inside the box that the march
+ * tests before the ray stops.  Unallocated corners mark nothing.  Marks are
+ * bytes set to 1; returns the number of evaluated samples. */
+long or_working_set(const or_scene *s, const float *rays, long n, uint8_t *m_grid, uint8_t *m_xy, uint8_t *m_xz,
+                    uint8_t *m_yz, uint8_t *m_occ, int nthreads)
+{
+    long samples = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    uint8_t *planes[3] = {m_xy, m_xz, m_yz};
+#pragma omp parallel reduction(+ : samples)
+    {
+        or_sample *smp = (or_sample *)malloc(sizeof(or_sample) * (size_t)(s->n_max > 0 ? s->n_max : 1));
+#pragma omp for schedule(dynamic, 64)
+        for (long r = 0; r < n; r++) {
+            const float *ray = rays + 6 * r;
+            or_march m;
+            march_ray(s, ray, smp, &m);
+            samples += m.count;
+            for (int i = 0; i < m.count; i++) {
+                or_stencil st;
+                make_stencil(s, smp[i].p, &st, NULL);
+                for (int c = 0; c < 8; c++)
+                    if (st.gidx[c] >= 0) mark(m_grid, st.gidx[c] / NCH);
+                for (int q = 0; q < 3; q++)
+                    for (int t = 0; t < 4; t++) mark(planes[q], st.pidx[q][t] / NCH);
+            }
+            /* the candidates the march tests: all in-box lattice samples up
+             * to the last evaluated one when the ray stopped early, else all */
+            double tin, tout;
+            if (!slab_range(s, ray, ray + 3, &tin, &tout)) continue;
+            double fklo = floor(tin / s->step) - 2.0, fkhi = ceil(tout / s->step) + 2.0;
+            if (fklo < 0.0) fklo = 0.0;
+            if (fkhi > 16777215.0) fkhi = 16777215.0;
+            int stopped = m.count > 0 && (m.count >= s->n_max || (s->t_thr > 0.0f && m.TN < (double)s->t_thr));
+            long khi = stopped ? (long)m.k_last : (long)fkhi;
+            for (long k = (long)fklo; k <= khi; k++) {
+                float p[3];
+                int cell = -1;
+                lattice_test(s, ray, ray + 3, k, p, &cell);
+                if (cell >= 0) mark(m_occ, cell);
+            }
+        }
+        free(smp);
+    }
+    return samples;
+}
