@@ -16,6 +16,7 @@ one JSON line with the max time over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -200,8 +201,16 @@ def cpu_baseline_sample(sc, cams, budget_s=12.0):
     t0 = time.perf_counter()
     oracle.render(osc, sample, nthreads=cores)
     dt = time.perf_counter() - t0
+    # the same oracle on one thread, on a sample a sixth of the CPU time
+    n1 = int(min(rays.shape[0], max(1024, budget_s / 6.0 / max(per_ray * cores, 1e-9))))
+    sample1 = rays[:: max(1, rays.shape[0] // n1)]
+    t0 = time.perf_counter()
+    oracle.render(osc, sample1, nthreads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": sample.shape[0] / dt / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
-            "sample": f"{sample.shape[0]} rays (every {stride}th ray of the 8 cameras), {dt:.1f} s"}
+            "sample": f"{sample.shape[0]} rays (every {stride}th ray of the 8 cameras), {dt:.1f} s",
+            "one_thread": {"value": sample1.shape[0] / dt1 / 1e6, "unit": "Mrays/s", "cores": 1,
+                           "sample": f"{sample1.shape[0]} rays (strided over the 8 cameras), {dt1:.1f} s"}}
 
 
 # ---------------------------------------------------------------------------
@@ -249,45 +258,72 @@ def bench_precision_render(om, torch, dev, steps, warmup, flush, stream):
     return out
 
 
-def bench_precision_train(om, torch, dev, steps, warmup, flush, stream, n_rays=1 << 20):
-    """Training fwd+bwd on 2^20 rays of 64 cameras, BF16 features (FP32 gradients)
-    vs FP32 features, 64x64x16 grid / 256^2, 256x32 planes."""
-    sc = synth.make_scene(5)
-    batch = synth.make_train_batch(5, n_rays)
-    rays_d = torch.as_tensor(batch["rays"]).to(dev)
-    dirs_d = torch.as_tensor(batch["smooth_dirs"]).to(dev)
-    tgt_d = torch.as_tensor(batch["target"]).to(dev)
+def _time_train(om, torch, scene, batch_d, lam, steps, warmup, flush, stream):
+    """Mean event time (ms) of one fused training step (fwd + bwd) on a batch
+    resident on the device; gradients zeroed and L2 flushed outside the events."""
+    rays_d, tgt_d, dirs_d = batch_d
+    n = rays_d.shape[0]
+    grads = om.zero_grads(scene)
+    saved = torch.empty(n * om.saved_bytes_per_ray() // 4, dtype=torch.float32, device=rays_d.device)
+    for _ in range(warmup):
+        om.train_step(scene, rays_d, tgt_d, dirs_d, lam=lam, grads=grads, saved=saved)
+    ms = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        for gt in grads.values():
+            gt.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        om.train_step(scene, rays_d, tgt_d, dirs_d, lam=lam, grads=grads, saved=saved)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    del grads, saved
+    return float(np.mean(ms))
+
+
+def _train_precisions(om, torch, dev, sc, batch, steps, warmup, flush, stream, table=None):
+    """BF16 vs FP32 features of one training workload: Mrays/s, feature bytes
+    and the peak of torch's device allocations (features, FP32 gradients,
+    batch, saved state)."""
+    n_rays = batch["rays"].shape[0]
+    batch_d = tuple(torch.as_tensor(batch[k]).to(dev) for k in ("rays", "target", "smooth_dirs"))
     lam = (1.0, 1e-2, 1e-4)
-    out = {"workload": "fwd+bwd 2^20 rays of 64 cameras, 64x64x16 grid, 256^2/256x32 planes, K=1",
-           "rays_per_step": n_rays,
-           "peak_device_bytes_note": "torch allocations of the form (features, FP32 gradients, rays, targets, "
-                                     "smoothness directions, saved state); the batch (~92 MB) is shared"}
+    out = {}
     for name, dt in (("bf16", torch.bfloat16), ("f32", torch.float32)):
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         torch.cuda.reset_peak_memory_stats(dev)
-        scene = om.scene_from_synth(sc, device=dev, feat_dtype=dt)
-        grads = om.zero_grads(scene)
-        saved = torch.empty(n_rays * om.saved_bytes_per_ray() // 4, dtype=torch.float32, device=dev)
-        for _ in range(warmup):
-            om.train_step(scene, rays_d, tgt_d, dirs_d, lam=lam, grads=grads, saved=saved)
-        ms = []
-        for _ in range(steps):
-            flush.fill_(1.0)
-            for gt in grads.values():
-                gt.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            om.train_step(scene, rays_d, tgt_d, dirs_d, lam=lam, grads=grads, saved=saved)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms.append(a.elapsed_time(b))
-        t = float(np.mean(ms))
+        scene = om.scene_from_synth(sc, device=dev, feat_dtype=dt, table=table)
+        t = _time_train(om, torch, scene, batch_d, lam, steps, warmup, flush, stream)
         feat_bytes = sum(x.numel() * x.element_size() for x in (scene.grid, scene.p_xy, scene.p_xz, scene.p_yz))
         out[name] = {"value": n_rays / (t * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": t,
                      "feature_bytes": feat_bytes,
                      "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev))}
-        del scene, grads, saved
+        del scene
+    return out
+
+
+def bench_precision_train(om, torch, dev, steps, warmup, flush, stream, n_rays=1 << 20):
+    """Training fwd+bwd on 2^20 rays of 64 cameras, BF16 features (FP32 gradients)
+    vs FP32 features: on the 64x64x16 heightfield scene (the literal sizes)
+    and at the city scene's sizes (512x512x32 brick grid, 2048^2 planes)."""
+    sc = synth.make_scene(5)
+    out = {"workload": "fwd+bwd 2^20 rays of 64 cameras, 64x64x16 grid, 256^2/256x32 planes, K=1",
+           "rays_per_step": n_rays,
+           "peak_device_bytes_note": "torch allocations of the form (features, FP32 gradients, rays, targets, "
+                                     "smoothness directions, saved state); the batch (~92 MB) is shared"}
+    out.update(_train_precisions(om, torch, dev, sc, synth.make_train_batch(5, n_rays), steps, warmup, flush,
+                                 stream))
+    spec = dataclasses.replace(synth.scene_spec(2), n_cams=64)
+    city = synth.make_scene(spec)
+    occ = torch.as_tensor(city["occ"]).to(dev)
+    table = om.build_brick_table(spec.aabb, spec.L, spec.brick, occ)[0].cpu().numpy()
+    out["city"] = {"workload": "fwd+bwd 2^20 rays of 64 oblique 1920x1080 cameras, sparse 512x512x32 grid "
+                               "(8^3 bricks), planes 2048^2 / 2048x128, occupancy 256^2, step 1/2048, K=1",
+                   "rays_per_step": n_rays}
+    out["city"].update(_train_precisions(om, torch, dev, city, synth.make_train_batch(spec, n_rays), steps, warmup,
+                                         flush, stream, table=table))
     return out
 
 

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from _util import GRAD_RTOL, gpu_scene, grad_errors
+from _util import GRAD_RTOL, brick_inputs, gpu_scene, grad_errors
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -241,3 +241,28 @@ def test_bf16_brick_grid_gradients():
                        lam=(1.0, 0.1, 0.01))
     np.testing.assert_allclose(float(res["loss"][0]), ref["loss"], rtol=1e-5)
     _check_grads(res, ref, what="bf16 brick")
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_city_scene_training(dtype):
+    """Training at the city scene's sizes (the large-scene reading of the big
+    training workload): 512x512x32 grid in 8^3 bricks, 2048^2 / 2048x128
+    planes, 256^2 occupancy, step 1/2048, rays from 64 oblique 1920x1080
+    cameras.  Every gradient tensor against the oracle (on the BF16-rounded
+    pool and planes for BF16)."""
+    spec = dataclasses.replace(synth.scene_spec(2), n_cams=64)
+    sc = synth.make_scene(spec)
+    table, pool = brick_inputs(sc)
+    sb = dict(sc, grid=pool, table=table)
+    if dtype == torch.bfloat16:
+        rb = lambda a: torch.as_tensor(a).to(torch.bfloat16).float().numpy()  # noqa: E731
+        sb.update(grid=rb(pool), p_xy=rb(sc["p_xy"]), p_xz=rb(sc["p_xz"]), p_yz=rb(sc["p_yz"]))
+    batch = _unambiguous(sb, synth.make_train_batch(spec, 8192))
+    scene = gpu_scene(sb, feat_dtype=dtype)
+    assert scene.brick == 8
+    res = om.train_step(scene, batch["rays"], batch["target"], batch["smooth_dirs"], lam=LAM)
+    torch.cuda.synchronize()
+    ref = oracle.train(oracle.OracleScene(sb), batch["rays"], batch["target"], batch["smooth_dirs"], lam=LAM)
+    assert np.count_nonzero(ref["grads"]["grid"]) > 10000
+    np.testing.assert_allclose(float(res["loss"][0]), ref["loss"], rtol=1e-5)
+    _check_grads(res, ref, what=f"city {dtype}")
