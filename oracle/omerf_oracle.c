@@ -504,6 +504,18 @@ void or_camera_rays(const float *cam, int W, int H, float *rays)
         }
 }
 
+/* threads of a parallel region: nthreads > 0 asks for that many for this
+ * call only, 0 for the OpenMP default */
+static int team_size(int nthreads)
+{
+#ifdef _OPENMP
+    return nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
 /* forward render of n rays [n][6].  Outputs (any may be NULL except rgb):
  * rgb [n][3], count [n], F [n][7], TN [n], ambiguous [n], k_first/k_last [n].
  * Returns the total number of unallocated-brick corner reads. */
@@ -511,12 +523,8 @@ long or_render(const or_scene *s, const float *rays, long n, double *rgb, int32_
                double *TN, int32_t *ambiguous, int32_t *k_first, int32_t *k_last, int nthreads)
 {
     long ua_total = 0;
-#ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#else
-    (void)nthreads;
-#endif
-#pragma omp parallel reduction(+ : ua_total)
+    const int nt = team_size(nthreads);
+#pragma omp parallel num_threads(nt) reduction(+ : ua_total)
     {
         or_sample *smp = (or_sample *)malloc(sizeof(or_sample) * (size_t)(s->n_max > 0 ? s->n_max : 1));
 #pragma omp for schedule(dynamic, 64)
@@ -961,13 +969,9 @@ long or_working_set(const or_scene *s, const float *rays, long n, uint8_t *m_gri
                     uint8_t *m_yz, uint8_t *m_occ, int nthreads)
 {
     long samples = 0;
-#ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#else
-    (void)nthreads;
-#endif
+    const int nt = team_size(nthreads);
     uint8_t *planes[3] = {m_xy, m_xz, m_yz};
-#pragma omp parallel reduction(+ : samples)
+#pragma omp parallel num_threads(nt) reduction(+ : samples)
     {
         or_sample *smp = (or_sample *)malloc(sizeof(or_sample) * (size_t)(s->n_max > 0 ? s->n_max : 1));
 #pragma omp for schedule(dynamic, 64)
