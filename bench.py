@@ -288,18 +288,20 @@ def _train_precisions(om, torch, dev, sc, batch, steps, warmup, flush, stream, t
     batch, saved state)."""
     n_rays = batch["rays"].shape[0]
     batch_d = tuple(torch.as_tensor(batch[k]).to(dev) for k in ("rays", "target", "smooth_dirs"))
+    batch_bytes = sum(x.numel() * x.element_size() for x in batch_d)
     lam = (1.0, 1e-2, 1e-4)
     out = {}
     for name, dt in (("bf16", torch.bfloat16), ("f32", torch.float32)):
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         torch.cuda.reset_peak_memory_stats(dev)
+        base = torch.cuda.memory_allocated(dev)
         scene = om.scene_from_synth(sc, device=dev, feat_dtype=dt, table=table)
         t = _time_train(om, torch, scene, batch_d, lam, steps, warmup, flush, stream)
         feat_bytes = sum(x.numel() * x.element_size() for x in (scene.grid, scene.p_xy, scene.p_xz, scene.p_yz))
         out[name] = {"value": n_rays / (t * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": t,
                      "feature_bytes": feat_bytes,
-                     "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev))}
+                     "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev) - base) + batch_bytes}
         del scene
     return out
 
@@ -311,8 +313,9 @@ def bench_precision_train(om, torch, dev, steps, warmup, flush, stream, n_rays=1
     sc = synth.make_scene(5)
     out = {"workload": "fwd+bwd 2^20 rays of 64 cameras, 64x64x16 grid, 256^2/256x32 planes, K=1",
            "rays_per_step": n_rays,
-           "peak_device_bytes_note": "torch allocations of the form (features, FP32 gradients, rays, targets, "
-                                     "smoothness directions, saved state); the batch (~92 MB) is shared"}
+           "peak_device_bytes_note": "the workload's own peak device allocations: scene (features, occupancy, "
+                                     "MLP, brick table), FP32 gradients, saved state and the batch (rays, "
+                                     "targets, smoothness directions)"}
     out.update(_train_precisions(om, torch, dev, sc, synth.make_train_batch(5, n_rays), steps, warmup, flush,
                                  stream))
     spec = dataclasses.replace(synth.scene_spec(2), n_cams=64)
