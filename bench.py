@@ -210,7 +210,40 @@ def cpu_baseline_sample(sc, cams, budget_s=12.0):
     return {"value": sample.shape[0] / dt / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
             "sample": f"{sample.shape[0]} rays (every {stride}th ray of the 8 cameras), {dt:.1f} s",
             "one_thread": {"value": sample1.shape[0] / dt1 / 1e6, "unit": "Mrays/s", "cores": 1,
-                           "sample": f"{sample1.shape[0]} rays (strided over the 8 cameras), {dt1:.1f} s"}}
+                           "sample": f"{sample1.shape[0]} rays (strided over the 8 cameras), {dt1:.1f} s"},
+            "render_4k": _oracle_render_4k(cores), "train": _oracle_train()}
+
+
+def _oracle_render_4k(cores, n=1 << 18):
+    """The oracle on a strided 2^18-pixel sample of the four 3840x2160 cameras
+    (FP32-valued features of the 1024x1024x64 city scene)."""
+    import oracle
+
+    sc = synth.make_scene(4)
+    table = oracle.brick_table(sc["spec"], sc["occ"])
+    osc = oracle.OracleScene(dict(sc, grid=synth.fill_brick_pool(sc, table), table=table))
+    rays = np.concatenate([oracle.camera_rays(c) for c in synth.make_cameras(4)])
+    sample = rays[:: rays.shape[0] // n]
+    t0 = time.perf_counter()
+    oracle.render(osc, sample, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample.shape[0] / dt / 1e6, "unit": "Mrays/s", "cores": cores,
+            "sample": f"{sample.shape[0]} rays strided over the 4 cameras, {dt:.1f} s"}
+
+
+def _oracle_train(n=1 << 15):
+    """The oracle's loss and analytic gradient (one thread: it sums into one
+    set of gradient arrays) on 2^15 rays of the 2^18-ray training batch."""
+    import oracle
+
+    sc = synth.make_scene(3)
+    b = synth.make_train_batch(3, 1 << 18)
+    sl = slice(0, 1 << 18, (1 << 18) // n)
+    t0 = time.perf_counter()
+    oracle.train(oracle.OracleScene(sc), b["rays"][sl], b["target"][sl], b["smooth_dirs"][sl], lam=(1.0, 1e-2, 1e-4))
+    dt = time.perf_counter() - t0
+    return {"value": n / dt / 1e6, "unit": "Mrays/s fwd+bwd", "cores": 1,
+            "sample": f"{n} rays strided over the 2^18-ray batch, {dt:.1f} s"}
 
 
 # ---------------------------------------------------------------------------
