@@ -152,7 +152,10 @@ omerf_status omerf_ray_interval(const omerf_scene *scene, const omerf_camera *ca
  *     w_i = T_i M_i alpha_i,  T_{i+1} = T_i (1 - M_i alpha_i),
  * and rgb = bg for a ray with no evaluated sample.
  *   cam    host camera (n == width * height, rays NULL), or NULL
- *   rays   device [n][6] float32 when cam is NULL
+ *   rays   device [n][6] float32 when cam is NULL: origin, unit direction,
+ *          finite (device data is not validated on the host; a ray with a
+ *          non-finite component evaluates no sample but may test up to
+ *          2^24 lattice candidates, which is slow)
  *   rgb    float32 [n][3] (output): device memory, or page-locked host memory
  *          (cudaHostAlloc / cudaHostRegister), which the kernel writes
  *          directly (on Grace-Blackwell over the coherent chip-to-chip link),
