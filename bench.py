@@ -40,7 +40,7 @@ BYTES_PER_RAY_RENDER = 12 + 4                          # rgb + count written
 # 1920x1080 cameras), from the ncu capture summarised in
 # profiles/march_fwd_render1080x8_sparse_f32.md; set to None whenever that
 # kernel changes until it is captured again.
-TRAFFIC_PER_LAUNCH = 172457984.0 + 175561216.0
+TRAFFIC_PER_LAUNCH = 173514752.0 + 175969536.0
 
 
 def _peaks():
