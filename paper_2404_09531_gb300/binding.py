@@ -714,3 +714,84 @@ class Trainer:
         adam_step(groups, self.step_no, beta1=self.betas[0], beta2=self.betas[1], eps=self.eps)
         self.scene.update()
         return res["loss"]
+
+    # ------------------------------------------------------------ checkpointing
+    _SETTINGS = ("total", "lr", "lr_occ", "lam_rgb", "lam_smooth", "lam_occ", "lam_sparsity", "lam_entropy",
+                 "betas", "eps")
+
+    def state_dict(self) -> dict:
+        """What resuming needs, as host arrays: the FP32 master parameters,
+        both Adam moments of every group, the iteration counter and the
+        optimiser settings.  (A BF16 scene's features are the rounded master.)"""
+        out = {"step_no": np.int64(self.step_no)}
+        for k in self._SETTINGS:
+            v = getattr(self, k)
+            out["setting/" + k] = np.asarray(np.nan if v is None else v, np.float64)
+        for k, p in self.master.items():
+            m, v = self.moments[k]
+            out["param/" + k] = p.detach().cpu().numpy()
+            out["m/" + k] = m.cpu().numpy()
+            out["v/" + k] = v.cpu().numpy()
+        return out
+
+    def load_state_dict(self, state: dict):
+        """Restore a state_dict into this trainer's tensors in place (shapes
+        must match), rewrite a BF16 scene's features from the master copy and
+        recompute the occupancy hull."""
+        for k, p in self.master.items():
+            for name, dst in (("param/", p), ("m/", self.moments[k][0]), ("v/", self.moments[k][1])):
+                src = np.asarray(state[name + k])
+                if tuple(src.shape) != tuple(dst.shape):
+                    raise OmerfError(f"checkpoint {name + k} has shape {src.shape}, expected {tuple(dst.shape)}")
+                dst.copy_(torch.as_tensor(src, dtype=torch.float32))
+            if self.shadow[k] is not None:
+                self.shadow[k].copy_(p)
+        for k in self._SETTINGS:
+            v = np.asarray(state["setting/" + k])
+            if k == "lam_occ" and np.isnan(v):
+                v = None
+            elif k == "total":
+                v = int(v)
+            elif v.ndim:
+                v = tuple(float(x) for x in v)
+            else:
+                v = float(v)
+            setattr(self, k, v)
+        self.step_no = int(state["step_no"])
+        self.scene.update()
+
+    def save(self, path):
+        """Write the scene's layout (box, grid and plane sizes, brick table,
+        plane z-range, march settings, feature dtype) and the state_dict to
+        one .npz file."""
+        sc = self.scene
+        meta = {"scene/aabb": np.asarray(sc.aabb, np.float32), "scene/grid_res": np.asarray(sc.grid_res, np.int32),
+                "scene/brick": np.int32(sc.brick),
+                "scene/march": np.asarray([sc.step, sc.eps, sc.t_thr, sc.n_max], np.float64),
+                "scene/bg": np.asarray(sc.bg, np.float32),
+                "scene/plane_z": np.asarray(sc.plane_z if sc.plane_z is not None else (np.nan, np.nan), np.float32),
+                "scene/bf16": np.int32(sc.feat_dtype == torch.bfloat16)}
+        if sc.table is not None:
+            meta["scene/table"] = sc.table.cpu().numpy()
+        np.savez(path, **meta, **self.state_dict())
+
+    @classmethod
+    def load(cls, path, device="cuda", stream=None) -> "Trainer":
+        """Rebuild the scene and its trainer from a file written by save()."""
+        z = np.load(path)
+        dev = torch.device(device)
+        dt = torch.bfloat16 if int(z["scene/bf16"]) else torch.float32
+        feats = {k: torch.as_tensor(z["param/" + k]).to(dev).to(dt).contiguous()
+                 for k in ("grid", "p_xy", "p_xz", "p_yz")}
+        step, eps, t_thr, n_max = (float(v) for v in z["scene/march"])
+        pz = z["scene/plane_z"]
+        scene = Scene(aabb=tuple(z["scene/aabb"]), grid=feats["grid"], p_xy=feats["p_xy"], p_xz=feats["p_xz"],
+                      p_yz=feats["p_yz"], occ=torch.as_tensor(z["param/occ"]).to(dev).contiguous(),
+                      mlp=torch.as_tensor(z["param/mlp"]).to(dev).contiguous(), step=step, eps=eps, t_thr=t_thr,
+                      n_max=int(n_max), bg=tuple(z["scene/bg"]),
+                      table=torch.as_tensor(z["scene/table"]).to(dev) if "scene/table" in z else None,
+                      brick=int(z["scene/brick"]), grid_res=tuple(int(v) for v in z["scene/grid_res"]),
+                      plane_z=None if np.isnan(pz).any() else tuple(pz), stream=stream)
+        tr = cls(scene)
+        tr.load_state_dict(dict(z))
+        return tr

@@ -87,3 +87,46 @@ def test_trainer_adds_the_regularisers_to_loss_and_gradients():
     for k in ("grid", "p_xy", "p_xz", "p_yz", "occ", "mlp"):
         a, b = tr.grads[k], res["grads"][k]
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-7 * float(b.abs().max()) + 1e-30), k
+
+
+@pytest.mark.parametrize("form", ["f32-dense", "bf16-bricks"])
+def test_checkpoint_resume(form, tmp_path):
+    """Train 3 steps, save, train 2 more; a trainer loaded from the file
+    repeats those 2 steps (losses and parameters equal up to the ordering of
+    float atomics), with the scene layout (brick table, dtype, march
+    settings) and the optimiser state (moments, step counter, schedules)
+    restored."""
+    if form == "f32-dense":
+        sc = synth.make_scene(3)
+        scene = om.scene_from_synth(sc, device="cuda")
+    else:
+        import dataclasses
+        sc = synth.make_scene(3)
+        spec = dataclasses.replace(sc["spec"], brick=8)
+        table = oracle.brick_table(spec, sc["occ"])
+        pool = oracle.extract_bricks(spec.L, 8, table, sc["grid"])
+        scene = om.scene_from_synth(dict(sc, spec=spec, grid=pool, table=table), device="cuda",
+                                    feat_dtype=torch.bfloat16)
+    batch = synth.make_train_batch(3, 1 << 13, seed=9)
+    pts = synth.sparsity_points(sc, 1 << 10)
+    erays = synth.entropy_rays(sc, 256)
+    tr = om.Trainer(scene, total_steps=100)
+    for _ in range(3):
+        tr.step(batch["rays"], batch["target"], batch["smooth_dirs"], sparsity_points=pts, entropy_rays=erays)
+    path = tmp_path / "ckpt.npz"
+    tr.save(path)
+    la = [float(tr.step(batch["rays"], batch["target"], batch["smooth_dirs"], sparsity_points=pts,
+                        entropy_rays=erays)[0]) for _ in range(2)]
+    tr2 = om.Trainer.load(path)
+    assert tr2.step_no == 3 and tr2.total == 100 and tr2.scene.brick == scene.brick
+    assert tr2.scene.feat_dtype == scene.feat_dtype
+    lb = [float(tr2.step(batch["rays"], batch["target"], batch["smooth_dirs"], sparsity_points=pts,
+                         entropy_rays=erays)[0]) for _ in range(2)]
+    np.testing.assert_allclose(lb, la, rtol=1e-5)
+    torch.cuda.synchronize()
+    for k in ("grid", "p_xy", "p_xz", "p_yz", "occ", "mlp"):
+        a, b = tr.master[k], tr2.master[k]
+        assert (a - b).abs().max().item() <= 1e-5 * max(a.abs().max().item(), 1.0), k
+    if form == "bf16-bricks":
+        assert torch.equal(tr2.scene.table, scene.table)
+        assert torch.equal(tr2.scene.grid, tr2.master["grid"].to(torch.bfloat16))
