@@ -80,7 +80,12 @@ typedef struct {
     float bg[3];               /* background colour added as T_N * bg */
     int32_t n_max;             /* maximum evaluated samples per ray (1..65536) */
     const void *grid;          /* device: dense grid or brick pool; 32-byte aligned (float32) or 16 (bfloat16) */
-    const int32_t *brick_table;/* device: brick table (brick grids only) */
+    const int32_t *brick_table;/* device: brick table (brick grids only): [nbx][nby][nbz] int32, pool
+                                  index or -1.  A sample reads its 8 corners through the brick of
+                                  its cell's lowest corner: when that brick is not stored, all 8
+                                  read as zero, even corners lying in a stored neighbour brick.
+                                  A table from omerf_build_brick_table (Sec. 4.4's rule, dilated
+                                  by one voxel) stores every brick an evaluated sample touches. */
     const void *plane_xy;      /* device, aligned like grid */
     const void *plane_xz;      /* device, aligned like grid */
     const void *plane_yz;      /* device, aligned like grid */
