@@ -35,12 +35,30 @@ import synth  # noqa: E402
 
 BYTES_PER_SAMPLE = {"f32": 640 + 8, "bf16": 320 + 8}  # feature gather + occupancy bounds
 BYTES_PER_RAY_RENDER = 12 + 4                          # rgb + count written
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel
-# (one launch of march_fwd_kernel<float, sparse, render> over the step's eight
-# 1920x1080 cameras), from the ncu capture summarised in
-# profiles/march_fwd_render1080x8_sparse_f32.md; set to None whenever that
-# kernel changes until it is captured again.
-TRAFFIC_PER_LAUNCH = 173514752.0 + 175969536.0
+# Sources the dominant kernel (march_fwd_kernel<float, sparse, render>) is
+# compiled from: a recorded DRAM traffic figure is valid only for the sources
+# it was captured with.
+RENDER_SOURCES = ("paper_2404_09531_gb300/csrc/march_fwd.cu", "paper_2404_09531_gb300/csrc/packed.cuh",
+                  "paper_2404_09531_gb300/csrc/common.cuh", "paper_2404_09531_gb300/csrc/mlp_mma.cuh")
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of that kernel
+# over the step's eight 1920x1080 cameras (one ncu capture), with the hash of
+# the sources it was captured from.
+TRAFFIC = {"sources_sha256_16": "752a45f5ea04f76d", "bytes": 173514752.0 + 175969536.0}
+
+
+def render_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in RENDER_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch():
+    """The recorded DRAM bytes per launch if the kernel's sources are the ones
+    it was captured from, else None."""
+    return TRAFFIC["bytes"] if render_sources_hash() == TRAFFIC["sources_sha256_16"] else None
 
 
 def _peaks():
@@ -199,7 +217,7 @@ def cpu_baseline_sample(sc, cams, budget_s=12.0):
     stride = max(1, rays.shape[0] // n)
     sample = rays[::stride]
     t0 = time.perf_counter()
-    oracle.render(osc, sample, nthreads=cores)
+    ref = oracle.render(osc, sample, nthreads=cores)
     dt = time.perf_counter() - t0
     # the same oracle on one thread, on a sample a sixth of the CPU time
     n1 = int(min(rays.shape[0], max(1024, budget_s / 6.0 / max(per_ray * cores, 1e-9))))
@@ -207,11 +225,12 @@ def cpu_baseline_sample(sc, cams, budget_s=12.0):
     t0 = time.perf_counter()
     oracle.render(osc, sample1, nthreads=1)
     dt1 = time.perf_counter() - t0
-    return {"value": sample.shape[0] / dt / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
-            "sample": f"{sample.shape[0]} rays (every {stride}th ray of the 8 cameras), {dt:.1f} s",
-            "one_thread": {"value": sample1.shape[0] / dt1 / 1e6, "unit": "Mrays/s", "cores": 1,
-                           "sample": f"{sample1.shape[0]} rays (strided over the 8 cameras), {dt1:.1f} s"},
-            "render_4k": _oracle_render_4k(cores), "train": _oracle_train()}
+    out = {"value": sample.shape[0] / dt / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+           "sample": f"{sample.shape[0]} rays (every {stride}th ray of the 8 cameras), {dt:.1f} s",
+           "one_thread": {"value": sample1.shape[0] / dt1 / 1e6, "unit": "Mrays/s", "cores": 1,
+                          "sample": f"{sample1.shape[0]} rays (strided over the 8 cameras), {dt1:.1f} s"},
+           "render_4k": _oracle_render_4k(cores), "train": _oracle_train()}
+    return out, ref, stride
 
 
 def _oracle_render_4k(cores, n=1 << 18):
@@ -244,6 +263,98 @@ def _oracle_train(n=1 << 15):
     dt = time.perf_counter() - t0
     return {"value": n / dt / 1e6, "unit": "Mrays/s fwd+bwd", "cores": 1,
             "sample": f"{n} rays strided over the 2^18-ray batch, {dt:.1f} s"}
+
+
+def _render_errors(rgb, count, ref):
+    """Error of GPU pixels against the FP64 oracle on the same rays: max-abs
+    and PSNR over rays the oracle does not flag as ambiguous at the
+    termination threshold, and the sample-count mismatches there."""
+    rgb = np.asarray(rgb, np.float64)
+    ok = ref["ambiguous"] == 0
+    err = np.abs(rgb[ok] - ref["rgb"][ok])
+    mse = float(np.mean(err ** 2)) if err.size else 0.0
+    out = {"rays": int(ok.size), "ambiguous": int((~ok).sum()), "max_abs": float(err.max(initial=0.0)),
+           "psnr_db": 10.0 * float(np.log10(1.0 / mse)) if mse > 0 else float("inf")}
+    if count is not None:
+        out["count_mismatch"] = int((np.asarray(count)[ok] != ref["count"][ok]).sum())
+    return out
+
+
+def _grad_errors(res, ref):
+    """Per tensor ||g_gpu - g_ref|| / ||g_ref|| against the oracle's analytic
+    gradient, the worst of them, and the loss's relative error."""
+    errs = {}
+    for k in ("grid", "p_xy", "p_xz", "p_yz", "occ", "mlp"):
+        a = res["grads"][k].double().cpu().numpy().reshape(-1)
+        b = np.asarray(ref["grads"][k], np.float64).reshape(-1)
+        nb = np.linalg.norm(b)
+        errs[k] = float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+    loss = float(res["loss"][0].item())
+    return {"grad_rel": errs, "grad_rel_max": max(errs.values()),
+            "loss_rel": abs(loss - ref["loss"]) / max(abs(ref["loss"]), 1e-30)}
+
+
+def oracle_errors_precision(om, torch, dev, n_render=1 << 16, n_train=8192):
+    """Every precision result against the FP64 oracle (this runs the oracle,
+    so it belongs to the CPU-baseline leg): the 4 x 3840x2160 render in BF16
+    and FP32 on a strided n_render-pixel sample (BF16 also against the oracle
+    on the BF16-rounded features, which isolates the arithmetic), and the
+    training gradients on an n_train-ray slice of each benchmarked batch."""
+    import oracle
+
+    rb = lambda a: torch.as_tensor(np.asarray(a, np.float32)).to(torch.bfloat16).float().numpy()  # noqa: E731
+    out = {}
+    sc = synth.make_scene(4)
+    table = oracle.brick_table(sc["spec"], sc["occ"])
+    pool = synth.fill_brick_pool(sc, table)
+    cams = synth.make_cameras(4)
+    rays = np.concatenate([oracle.camera_rays(c) for c in cams])
+    stride = rays.shape[0] // n_render
+    ref = oracle.render(oracle.OracleScene(dict(sc, grid=pool, table=table)), rays[::stride])
+    sc_b = dict(sc, grid=rb(pool), table=table, p_xy=rb(sc["p_xy"]), p_xz=rb(sc["p_xz"]), p_yz=rb(sc["p_yz"]))
+    ref_b = oracle.render(oracle.OracleScene(sc_b), rays[::stride])
+    for name, dt in (("bf16", torch.bfloat16), ("f32", torch.float32)):
+        scene = om.scene_from_synth(sc, device=dev, table=table, feat_dtype=dt)
+        rgb, cnt = om.render_cameras(scene, cams)
+        rgb, cnt = rgb[::stride].cpu().numpy(), cnt[::stride].cpu().numpy()
+        out[f"render_{name}"] = _render_errors(rgb, cnt, ref)
+        if name == "bf16":
+            out["render_bf16_vs_bf16_features"] = _render_errors(rgb, cnt, ref_b)
+        del scene
+    out["render_sample"] = f"every {stride}th pixel of the 4 cameras ({rays[::stride].shape[0]} rays)"
+    lam = (1.0, 1e-2, 1e-4)
+    # config 3 (FP32), oracle-rendered targets of the perturbed features
+    tsc = synth.make_scene(3)
+    b = synth.make_train_batch(3, 1 << 18)
+    sl = slice(0, n_train)
+    tgt = oracle.render(oracle.OracleScene(synth.perturb_scene(tsc)), b["rays"][sl])["rgb"].astype(np.float32)
+    scene = om.scene_from_synth(tsc, device=dev)
+    res = om.train_step(scene, b["rays"][sl], tgt, b["smooth_dirs"][sl], lam=lam)
+    out["train_f32"] = _grad_errors(res, oracle.train(oracle.OracleScene(tsc), b["rays"][sl], tgt,
+                                                      b["smooth_dirs"][sl], lam=lam))
+    # the 2^20-ray workloads: BF16 features against the oracle on the rounded
+    # features, and the city scene's sizes in FP32
+    sc5 = synth.make_scene(5)
+    b5 = synth.make_train_batch(5, 1 << 20)
+    scene = om.scene_from_synth(sc5, device=dev, feat_dtype=torch.bfloat16)
+    res = om.train_step(scene, b5["rays"][sl], b5["target"][sl], b5["smooth_dirs"][sl], lam=lam)
+    sc5b = dict(sc5, grid=rb(sc5["grid"]), p_xy=rb(sc5["p_xy"]), p_xz=rb(sc5["p_xz"]), p_yz=rb(sc5["p_yz"]))
+    out["train_bf16_vs_bf16_features"] = _grad_errors(res, oracle.train(oracle.OracleScene(sc5b), b5["rays"][sl],
+                                                                         b5["target"][sl], b5["smooth_dirs"][sl],
+                                                                         lam=lam))
+    spec = dataclasses.replace(synth.scene_spec(2), n_cams=64)
+    city = synth.make_scene(spec)
+    ctable = oracle.brick_table(spec, city["occ"])
+    cpool = synth.fill_brick_pool(city, ctable)
+    bc = synth.make_train_batch(spec, 1 << 20)
+    sl = slice(0, n_train // 2)
+    scene = om.scene_from_synth(city, device=dev, table=ctable)
+    res = om.train_step(scene, bc["rays"][sl], bc["target"][sl], bc["smooth_dirs"][sl], lam=lam)
+    out["train_city_f32"] = _grad_errors(res, oracle.train(oracle.OracleScene(dict(city, grid=cpool, table=ctable)),
+                                                           bc["rays"][sl], bc["target"][sl], bc["smooth_dirs"][sl],
+                                                           lam=lam))
+    out["train_sample"] = f"the first {n_train} rays of each batch ({n_train // 2} for the city scene)"
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -360,6 +471,35 @@ def bench_precision_train(om, torch, dev, steps, warmup, flush, stream, n_rays=1
                    "rays_per_step": n_rays}
     out["city"].update(_train_precisions(om, torch, dev, city, synth.make_train_batch(spec, n_rays), steps, warmup,
                                          flush, stream, table=table))
+    return out
+
+
+def measure_load_peaks(om, torch, dev, stream):
+    """Load bandwidth (bytes delivered to registers per second) of the
+    gather's 256-bit read-only load, measured with omerf_probe_load_bandwidth
+    in the march's launch shape (3 CTAs of 256 threads per SM): from L1
+    (a 16 KB slice per CTA, re-read 4000 times) and from L2 (a 160 KB slice
+    per CTA: 480 KB per SM, beyond L1; 73 MB in all, inside L2).  Best of 5
+    after 3 warm-up launches, CUDA events on the launching stream."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    ctas = 3 * sms
+    out = {}
+    for name, per_cta, passes in (("l1", 16384, 4000), ("l2", 163840, 100)):
+        buf = torch.rand(ctas * per_cta // 4, device=dev)
+        sink = torch.empty(ctas * 256, dtype=torch.float32, device=dev)
+        for _ in range(3):
+            om.probe_load_bandwidth(buf, per_cta, ctas, passes, sink)
+        best = float("inf")
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nbytes = om.probe_load_bandwidth(buf, per_cta, ctas, passes, sink)
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        out[name] = {"gbs": nbytes / (best * 1e-3) / 1e9, "ms": best, "ctas": ctas, "bytes_per_cta": per_cta,
+                     "passes": passes}
+        del buf, sink
     return out
 
 
@@ -566,6 +706,7 @@ def run_native(args):
     t_loop, t_adam = float(np.mean(loop_ms)), float(np.mean(adam_ms))
 
     extraction = bench_extraction(om, torch, scene, max(1, min(args.steps, 5)), args.warmup, flush, stream)
+    peaks = measure_load_peaks(om, torch, dev, stream)
 
     precision = None
     if not args.no_precision:
@@ -580,6 +721,7 @@ def run_native(args):
     t_launch = float(np.mean(per_launch)) * 1e-3
     bytes_launch = samples_per_step * BYTES_PER_SAMPLE["f32"] + rays_per_step * BYTES_PER_RAY_RENDER
     achieved = bytes_launch / t_launch / 1e9
+    l1, l2 = peaks["l1"]["gbs"], peaks["l2"]["gbs"]
     cfg = _workload_config()
     cfg["samples_per_step"] = samples_per_step
     cfg["mean_samples_per_ray"] = samples_per_step / rays_per_step
@@ -590,14 +732,24 @@ def run_native(args):
         "dtype": "f32", "data": "synthetic (seeded oblique city scene; paper datasets unavailable)",
         "config": cfg,
         "msamples_per_s": ws * samples_per_step / (t_step * 1e-3) / 1e6,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": TRAFFIC_PER_LAUNCH,
+        "roofline": {"bound": "l1", "achieved": achieved, "peak": l1, "unit": "GB/s", "frac": achieved / l1,
+                     "traffic": traffic_per_launch(),
                      "kernel": "march_fwd_kernel<float, sparse, render>",
-                     "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                     "peak_kind": "measured in this run: L1 load bandwidth of the gather's 256-bit read-only load "
+                                  "(omerf_probe_load_bandwidth, 3 x 256-thread CTAs per SM, 16 KB slice each)",
                      "algorithmic_bytes_per_launch": bytes_launch,
-                     "note": "the 648 B/sample feature gather is served from L1 (85-88 % hits) and L2 (97 %); "
-                             "DRAM moves only the frame's working set (traffic), so frac exceeds 1; the "
-                             "binding unit is the L1 data pipe, 77-83 % busy under ncu"},
+                     "algorithmic_bytes": "648 B per evaluated sample (8 grid corners + 12 plane texels x 32 B, "
+                                          "+ 8 B occupancy bounds) + 16 B per ray written",
+                     "l2": {"peak": l2, "frac": achieved / l2, "peak_kind": "measured in this run: the same "
+                            "probe, a 160 KB slice per CTA (beyond L1, inside L2)"},
+                     "hbm": {"peak": hbm, "frac": achieved / hbm, "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                             "traffic_frac": (traffic_per_launch() / t_launch / 1e9 / hbm)
+                             if traffic_per_launch() else None},
+                     "probes": peaks,
+                     "note": "the gather is served from L1 (85-88 % hits) and L2 (97 %): the algorithmic bytes "
+                             "are bytes delivered to registers, bounded by L1's load bandwidth; DRAM moves only "
+                             "each frame's working set (traffic: null when the kernel's sources differ from "
+                             "those of the recorded ncu capture)"},
         "e2e": {"value": ws * rays_per_step / (e2e_step * 1e-3) / 1e6, "unit": "Mrays/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "train": {"metric": "Mrays/s fwd+bwd train", "value": (1 << 18) / (t_train * 1e-3) / 1e6,
@@ -617,10 +769,19 @@ def run_native(args):
         "gpu_launches": args.steps,
         "clocks": clk,
     }
+    if not args.no_cpu_baseline:
+        # the oracle's timing, and its outputs on the same samples: every
+        # result's error against FP64
+        line["cpu_baseline"], ref, stride = cpu_baseline_sample(sc, cams)
+        rgb_all, cnt_all = om.render_cameras(scene, cams)
+        line["error_vs_oracle"] = _render_errors(rgb_all[::stride].cpu().numpy(), cnt_all[::stride].cpu().numpy(),
+                                                 ref)
+        line["error_vs_oracle"]["sample"] = line["cpu_baseline"]["sample"]
+        del rgb_all, cnt_all
+        if precision is not None:
+            precision["vs_oracle"] = oracle_errors_precision(om, torch, dev)
     if precision is not None:
         line["precision"] = precision
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(sc, cams)
     print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -58,7 +58,7 @@ typedef enum {
     OMERF_ESHAPE = -2,   /* inconsistent sizes */
     OMERF_EDEVICE = -3,  /* no usable CUDA device, or a pointer is not device memory */
     OMERF_ECUDA = -4,    /* a CUDA runtime call failed */
-    OMERF_ETIMEOUT = -5, /* omerf_sync gave up waiting */
+    OMERF_ETIMEOUT = -5, /* omerf_sync gave up waiting, or a bounded device-side wait ran out */
     OMERF_ENOMEM = -6    /* the library could not allocate its own state */
 } omerf_status;
 
@@ -81,11 +81,13 @@ typedef struct {
     int32_t n_max;             /* maximum evaluated samples per ray (1..65536) */
     const void *grid;          /* device: dense grid or brick pool; 32-byte aligned (float32) or 16 (bfloat16) */
     const int32_t *brick_table;/* device: brick table (brick grids only): [nbx][nby][nbz] int32, pool
-                                  index or -1.  A sample reads its 8 corners through the brick of
-                                  its cell's lowest corner: when that brick is not stored, all 8
-                                  read as zero, even corners lying in a stored neighbour brick.
-                                  A table from omerf_build_brick_table (Sec. 4.4's rule, dilated
-                                  by one voxel) stores every brick an evaluated sample touches. */
+                                  index or -1.  Each of a sample's 8 corner vertices is read
+                                  through the brick that holds it; a vertex of a brick that is not
+                                  stored reads as zero (and receives no gradient).  Any table is
+                                  accepted; one from omerf_build_brick_table (Sec. 4.4's rule,
+                                  dilated by one voxel) stores every brick an evaluated sample
+                                  touches, and omerf_grow_brick_table extends a table after the
+                                  occupancy plane has moved. */
     const void *plane_xy;      /* device, aligned like grid */
     const void *plane_xz;      /* device, aligned like grid */
     const void *plane_yz;      /* device, aligned like grid */
@@ -112,7 +114,8 @@ typedef struct omerf_scene omerf_scene;
 /* Create a scene handle from a description (validated on the host).  The
  * handle owns small device state only: the occupancy hull and coarse
  * max-pooled occupancy grid used to skip empty space, per-launch work
- * counters and, for a brick grid, one neighbour record per brick.  It builds
+ * counters and, for a brick grid, one 32-byte neighbour record per brick of
+ * the grid (nbx * nby * nbz, stored or not).  It builds
  * that state on `stream`; for a brick grid it then waits for the stream and
  * checks that every table entry is -1 or a valid pool index (OMERF_ESHAPE
  * otherwise).  Errors: OMERF_EINVAL / OMERF_ESHAPE for bad descriptions,
@@ -140,6 +143,24 @@ void omerf_scene_destroy(omerf_scene *scene);
 omerf_status omerf_build_brick_table(const float aabb[6], const int32_t grid_res[3], int32_t brick,
                                      const float *occ, int32_t occ_res, int32_t *table,
                                      int32_t *n_alloc, void *stream);
+
+/* Grow a brick table after the occupancy plane has moved (training moves
+ * z_min and z_max, so the bricks Sec. 4.4's rule stores change): table =
+ * the bricks old_table stores plus the bricks the rule of
+ * omerf_build_brick_table allocates for occ, pool indices reassigned in
+ * x-major brick order (re-extract the pool with omerf_extract_bricks from the
+ * old pool and old_table).  Bricks are never dropped, so the features
+ * trained so far are kept.
+ *   old_table  device int32 [nbx][nby][nbz]: entries -1 or >= 0
+ *   table      device int32, same shape (output; must not be old_table)
+ *   n_alloc    device int32 scalar (output): bricks in table
+ *   missing    device int32 scalar (output): bricks the rule allocates that
+ *              old_table does not store; 0 means old_table already covers
+ *              the rule (table then stores the same bricks)
+ * Errors as omerf_build_brick_table.  Two kernel launches and a memset. */
+omerf_status omerf_grow_brick_table(const float aabb[6], const int32_t grid_res[3], int32_t brick,
+                                    const float *occ, int32_t occ_res, const int32_t *old_table,
+                                    int32_t *table, int32_t *n_alloc, int32_t *missing, void *stream);
 
 /* Ray interval (box and occupancy-slab intersection, Sec. 4.4's bounding-box
  * skipping): for each ray, the inclusive lattice index range [k_lo, k_hi]
@@ -179,15 +200,22 @@ omerf_status omerf_render(const omerf_scene *scene, const omerf_camera *cam, con
  * fixed buffers, or a frame loop that cannot afford cudaMalloc, which may
  * synchronise the device.  It takes the scene description directly (no
  * handle) and keeps its scratch (work counters, occupancy hulls, brick
- * neighbour records) in a 1 MiB static __device__ array that every GPU
+ * neighbour records) in an 8 MiB static __device__ array that every GPU
  * loading this library holds until the process exits.  Arguments, layouts
  * and results are those of omerf_render.
  *   - The first call on a device looks up the array's device address with
  *     that device current; make that first call before any stream capture.
+ *     The address is kept for the life of the process: do not call this
+ *     entry point on a device after cudaDeviceReset on it.
+ *   - Pointers are checked as omerf_scene_create and omerf_render check them:
+ *     the description's arrays must be device memory (OMERF_EDEVICE
+ *     otherwise), rgb and count device or page-locked host memory.
  *   - Scenes whose scratch does not fit are rejected with OMERF_ESHAPE: the
  *     coarse occupancy grid takes 8 bytes per cell (ceil(M / 2^l)^2 cells, l
- *     the smallest level whose cells span a 32-sample lattice window) and a
- *     brick grid 32 bytes per brick; together at most 1,044,224 bytes.
+ *     the smallest level whose cells span a 32-sample lattice window,
+ *     rounded up to 256 bytes) and a brick grid 32 bytes per brick of the
+ *     grid, stored or not (nbx * nby * nbz); together at most 8,384,256
+ *     bytes.
  *   - Every call reuses the same array: calls whose kernels overlap on the GPU
  *     (different streams, or several host threads) race and give wrong
  *     results.  Order them on one stream.
@@ -367,6 +395,22 @@ float omerf_lr_exponential(float lr0, float lr1, int64_t step, int64_t total);
 /* Occupancy-loss weight lambda_7 of appendix A: 0 before iteration 10,000,
  * then 1e-4 multiplied by 1.5 every 2,000 iterations, at most 0.2.  Host-only. */
 float omerf_lambda_occ(int64_t step);
+
+/* Load-bandwidth probe (the paper has no counterpart: a measurement tool
+ * for the roofline of the march, whose feature gather is served from L1 and
+ * L2).  ctas CTAs of 256 threads each read their own bytes_per_cta-byte
+ * slice of buf `passes` times with the gather's 256-bit read-only load, a
+ * warp's load covering 1 KB contiguous; bytes delivered to registers =
+ * ctas * bytes_per_cta * passes.  A slice that fits in L1 (with the CTAs
+ * resident on one SM) measures L1's load bandwidth, a larger one inside L2
+ * measures L2's.
+ *   buf   device float32, ctas * bytes_per_cta bytes, 32-byte aligned
+ *   bytes_per_cta  a positive multiple of 8192, at most 2^30
+ *   sink  device float32 [ctas * 256] (output: per-thread sums, so that the
+ *         loads are not removed)
+ * One kernel launch. */
+omerf_status omerf_probe_load_bandwidth(const float *buf, int64_t bytes_per_cta, int32_t ctas, int32_t passes,
+                                        float *sink, void *stream);
 
 /* Wait for `stream` with a bounded host-side poll; returns OMERF_ETIMEOUT
  * after timeout_ms milliseconds (< 0 waits without limit), OMERF_ECUDA if

@@ -66,6 +66,7 @@ SIGNATURES = {
     "omerf_scene_update": (ctypes.c_int, [_P, _P]),
     "omerf_scene_destroy": (None, [_P]),
     "omerf_build_brick_table": (ctypes.c_int, [_P, _P, _I, _P, _I, _P, _P, _P]),
+    "omerf_grow_brick_table": (ctypes.c_int, [_P, _P, _I, _P, _I, _P, _P, _P, _P, _P]),
     "omerf_ray_interval": (ctypes.c_int, [_P, _P, _P, _L, _P, _P]),
     "omerf_render": (ctypes.c_int, [_P, _P, _P, _L, _P, _P, _P]),
     "omerf_render_noalloc": (ctypes.c_int, [_P, _P, _P, _L, _P, _P, _P]),
@@ -84,6 +85,7 @@ SIGNATURES = {
     "omerf_adam_step": (ctypes.c_int, [_P, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, _L, _P]),
     "omerf_lr_exponential": (ctypes.c_float, [ctypes.c_float, ctypes.c_float, _L, _L]),
     "omerf_lambda_occ": (ctypes.c_float, [_L]),
+    "omerf_probe_load_bandwidth": (ctypes.c_int, [_P, _L, _I, _I, _P, _P]),
     "omerf_sync": (ctypes.c_int, [_P, _I]),
     "omerf_last_error": (ctypes.c_char_p, []),
 }
@@ -244,6 +246,21 @@ def build_brick_table(aabb, grid_res, brick, occ: torch.Tensor, stream=None):
     _check(lib().omerf_build_brick_table(a, g, int(brick), _ptr(occ), int(occ.shape[0]), _ptr(table),
                                          _ptr(n_alloc), _stream(stream)), "omerf_build_brick_table")
     return table, n_alloc
+
+
+def grow_brick_table(aabb, grid_res, brick, occ: torch.Tensor, old_table: torch.Tensor, stream=None):
+    """The stored bricks of ``old_table`` plus those Sec. 4.4's rule allocates
+    for ``occ`` -> (table, n_alloc tensor, missing tensor: bricks added)."""
+    _require_cuda(occ, "occ")
+    _require_cuda(old_table, "old_table")
+    table = torch.empty_like(old_table)
+    n_alloc = torch.empty(1, dtype=torch.int32, device=occ.device)
+    missing = torch.empty(1, dtype=torch.int32, device=occ.device)
+    a = (ctypes.c_float * 6)(*[float(v) for v in aabb])
+    g = (ctypes.c_int32 * 3)(*[int(v) for v in grid_res])
+    _check(lib().omerf_grow_brick_table(a, g, int(brick), _ptr(occ), int(occ.shape[0]), _ptr(old_table), _ptr(table),
+                                        _ptr(n_alloc), _ptr(missing), _stream(stream)), "omerf_grow_brick_table")
+    return table, n_alloc, missing
 
 
 def scene_from_synth(sc: dict, device="cuda", feat_dtype=None, table=None, stream=None, **over) -> Scene:
@@ -615,6 +632,19 @@ def lambda_occ(step):
     return float(lib().omerf_lambda_occ(int(step)))
 
 
+def probe_load_bandwidth(buf: torch.Tensor, bytes_per_cta: int, ctas: int, passes: int, sink=None, stream=None):
+    """Launch the load-bandwidth probe over ``buf`` (float32, at least
+    ctas * bytes_per_cta bytes); returns the bytes it delivers to registers."""
+    _require_cuda(buf, "buf")
+    if buf.dtype != torch.float32 or buf.numel() * 4 < int(ctas) * int(bytes_per_cta):
+        raise OmerfError("buf must be float32 with at least ctas * bytes_per_cta bytes")
+    if sink is None:
+        sink = torch.empty(int(ctas) * 256, dtype=torch.float32, device=buf.device)
+    _check(lib().omerf_probe_load_bandwidth(_ptr(buf), int(bytes_per_cta), int(ctas), int(passes), _ptr(sink),
+                                            _stream(stream)), "omerf_probe_load_bandwidth")
+    return int(ctas) * int(bytes_per_cta) * int(passes)
+
+
 def sync(stream=None, timeout_ms=-1):
     """Bounded wait for a stream (raises OmerfError on timeout or CUDA error)."""
     _check(lib().omerf_sync(_stream(stream), int(timeout_ms)), "omerf_sync")
@@ -665,8 +695,10 @@ class Trainer:
 
     def __init__(self, scene: Scene, total_steps=80000, lr=(1e-2, 1e-3), lr_occ=(5e-5, 1e-5), lam_rgb=1.0,
                  lam_smooth=0.1, lam_occ=None, lam_sparsity=0.05, lam_entropy=1e-3, betas=(0.9, 0.99),
-                 eps=1e-15):
+                 eps=1e-15, grow_bricks_every=1):
         self.scene = scene
+        self.grow_bricks_every = int(grow_bricks_every)
+        self.bricks_grown = 0
         self.total = int(total_steps)
         self.lr, self.lr_occ = lr, lr_occ
         self.lam_rgb, self.lam_smooth, self.lam_occ = lam_rgb, lam_smooth, lam_occ
@@ -713,11 +745,48 @@ class Trainer:
         self.step_no += 1
         adam_step(groups, self.step_no, beta1=self.betas[0], beta2=self.betas[1], eps=self.eps)
         self.scene.update()
+        if self.scene.brick and self.grow_bricks_every > 0 and self.step_no % self.grow_bricks_every == 0:
+            self.grow_bricks()
         return res["loss"]
+
+    def grow_bricks(self, stream=None) -> bool:
+        """Store the bricks Sec. 4.4's rule now wants for the moved occupancy
+        plane (brick scenes): the table grows (no brick is dropped), the FP32
+        master grid, both Adam moments and the scene's features are
+        re-extracted into the new pool layout (new bricks start at zero) and
+        the trainer's scene is rebuilt over them.  One 4-byte readback; returns
+        True if the table grew."""
+        sc = self.scene
+        if not sc.brick:
+            return False
+        table, n_alloc, missing = grow_brick_table(sc.aabb, sc.grid_res, sc.brick, sc.occ, sc.table, stream)
+        if int(missing.item()) == 0:
+            return False
+        nb = int(n_alloc.item())
+
+        def remap(t):
+            return extract_bricks(sc.grid_res, sc.brick, table, t, src_table=sc.table, n_bricks=nb,
+                                  src_n_bricks=int(t.shape[0]), stream=stream)
+
+        master = remap(self.master["grid"])
+        m, v = (remap(t) for t in self.moments["grid"])
+        grid = master if self.shadow["grid"] is None else remap(sc.grid)
+        new = Scene(aabb=sc.aabb, grid=grid, table=table, brick=sc.brick, grid_res=sc.grid_res, p_xy=sc.p_xy,
+                    p_xz=sc.p_xz, p_yz=sc.p_yz, occ=sc.occ, mlp=sc.mlp, step=sc.step, eps=sc.eps, t_thr=sc.t_thr,
+                    n_max=sc.n_max, bg=sc.bg, plane_z=sc.plane_z, stream=stream)
+        self.master["grid"] = master
+        if self.shadow["grid"] is not None:
+            self.shadow["grid"] = grid
+        self.moments["grid"] = (m, v)
+        self.grads["grid"] = torch.zeros(grid.shape, dtype=torch.float32, device=grid.device)
+        self.scene = new
+        sc.close()
+        self.bricks_grown += 1
+        return True
 
     # ------------------------------------------------------------ checkpointing
     _SETTINGS = ("total", "lr", "lr_occ", "lam_rgb", "lam_smooth", "lam_occ", "lam_sparsity", "lam_entropy",
-                 "betas", "eps")
+                 "betas", "eps", "grow_bricks_every")
 
     def state_dict(self) -> dict:
         """What resuming needs, as host arrays: the FP32 master parameters,
@@ -747,10 +816,12 @@ class Trainer:
             if self.shadow[k] is not None:
                 self.shadow[k].copy_(p)
         for k in self._SETTINGS:
+            if "setting/" + k not in state:
+                continue  # a checkpoint written before the setting existed
             v = np.asarray(state["setting/" + k])
             if k == "lam_occ" and np.isnan(v):
                 v = None
-            elif k == "total":
+            elif k in ("total", "grow_bricks_every"):
                 v = int(v)
             elif v.ndim:
                 v = tuple(float(x) for x in v)

@@ -43,7 +43,7 @@ struct Geo {
   const float2* occ;
   const float* mlp;
   const float* hull;       // device [2]: min z_min, max z_max over non-empty cells
-  const int* nbr;          // device [n_bricks][8]: pool index of brick b's (+dx, +dy, +dz) neighbours
+  const int* nbr;          // device [nbx * nby * nbz][8]: pool index of the (+dx, +dy, +dz) neighbours
   const float2* chull;     // device [Mc][Mc]: coarse max-pooled (min z_min, max z_max)
   int clog2;               // coarse cell = 2^clog2 x 2^clog2 occupancy cells
   int Mc;                  // coarse cells per axis
@@ -270,19 +270,22 @@ __device__ __forceinline__ void grid_stencil(const Geo& g, const float p[3], int
 #pragma unroll
     for (int c = 0; c < 8; c++) off[c] = base + ((c >> 2) & 1) * sx + ((c >> 1) & 1) * sy + (c & 1) * sz;
   } else {
-    // brick grid: the base brick's pool index, then its neighbour record
-    // (one 256-bit read) gives the brick of every corner without branching
+    // brick grid: a cell inside its brick reads all corners from the brick's
+    // table entry; a cell reaching into neighbour bricks reads the record of
+    // its lowest corner's brick (one 256-bit load: the pool index of the
+    // brick of every corner, stored or not), so every corner is read through
+    // its own brick without branching on which ones are stored
     const int s = g.blog2, m = (1 << s) - 1, B = 1 << s;
-    const int b0 = __ldg(g.table + ((i[0] >> s) * g.nb[1] + (i[1] >> s)) * g.nb[2] + (i[2] >> s));
+    const int lin = ((i[0] >> s) * g.nb[1] + (i[1] >> s)) * g.nb[2] + (i[2] >> s);
     const int cx = (i[0] & m) == m, cy = (i[1] & m) == m, cz = (i[2] & m) == m;
     int nb[8];
-    if (b0 >= 0 && (cx | cy | cz)) {
+    if (cx | cy | cz) {
       asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                    : "=r"(nb[0]), "=r"(nb[1]), "=r"(nb[2]), "=r"(nb[3]), "=r"(nb[4]), "=r"(nb[5]), "=r"(nb[6]),
                      "=r"(nb[7])
-                   : "l"(g.nbr + 8 * b0));
+                   : "l"(g.nbr + 8 * lin));
     } else {
-      // every corner of a cell inside the brick is in the brick itself
+      const int b0 = __ldg(g.table + lin);
 #pragma unroll
       for (int c = 0; c < 8; c++) nb[c] = b0;
     }

@@ -96,17 +96,35 @@ __global__ void __launch_bounds__(256) extract_bricks_kernel(int Lx, int Ly, int
 // into shared memory (vertices beyond the grid arrive as zeros) and one bulk
 // store writes it to its pool slot.  One thread per CTA drives the copies
 // through two buffers: the store of one brick overlaps the load of the
-// next.  Every wait on the load's mbarrier is bounded; a CTA that runs out
-// of tries stops.
+// next.  Every wait on the load's mbarrier is bounded: a CTA whose wait runs
+// out of tries (wait_tries, 2^20 normally) ORs kErrExtractWait into the
+// error word, waits (again bounded) for the load still in flight so that no
+// copy lands in the shared memory of a finished CTA, and stops; the host
+// reports the word as OMERF_ETIMEOUT.
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Poll an mbarrier phase at most `tries` times; true once it has completed.
+__device__ __forceinline__ bool wait_parity(unsigned bar, unsigned phase, int tries) {
+  for (int t = 0; t < tries; t++) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
 }
 
 __global__ void __launch_bounds__(32) extract_bricks_tma_kernel(const __grid_constant__ CUtensorMap src, int nbx,
                                                                int nby, int nbz, int B,
                                                                const int* __restrict__ table, int n_bricks,
                                                                unsigned char* __restrict__ pool,
-                                                               unsigned brick_bytes) {
+                                                               unsigned brick_bytes, int wait_tries,
+                                                               unsigned* err) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long bar[2];
   if (threadIdx.x != 0) return;
@@ -134,17 +152,15 @@ __global__ void __launch_bounds__(32) extract_bricks_tma_kernel(const __grid_con
         "%5}], [%6];" ::"r"(dst),
         "l"(&src), "r"(0), "r"(bk * B), "r"(bj * B), "r"(bi * B), "r"(bar_s)
         : "memory");
-    bool done = false;
-    for (int tries = 0; tries < (1 << 20) && !done; tries++) {
-      unsigned ok;
-      asm volatile(
-          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-          : "=r"(ok)
-          : "r"(bar_s), "r"(phase[slot])
-          : "memory");
-      done = ok != 0u;
+    if (!wait_parity(bar_s, phase[slot], wait_tries)) {
+      // give up on this brick: report, let the load in flight land, stop
+      const bool drained = wait_parity(bar_s, phase[slot], 1 << 20);
+      if (err) {
+        atomicOr_system(err, kErrExtractWait | (drained ? 0u : kErrExtractDrain));
+        __threadfence_system();
+      }
+      break;
     }
-    if (!done) break;  // the load never completed: stop rather than wait forever
     phase[slot] ^= 1u;
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(pool + (size_t)b * brick_bytes),
                  "r"(dst), "r"(brick_bytes)
@@ -255,6 +271,7 @@ int sm_count() {
 
 omerf_status omerf_occupancy_grid(const float aabb[6], const float* occ, int32_t M, const int32_t N[3],
                                   uint32_t* bits, unsigned long long* count, void* stream) {
+  OMERF_API_RANGE();
   if (!aabb || !N || !occ || !bits) { set_error("NULL argument"); return OMERF_EINVAL; }
   if (M < 1 || N[0] < 1 || N[1] < 1 || N[2] < 1) { set_error("M and N must be >= 1"); return OMERF_ESHAPE; }
   if (!(aabb[4] < aabb[5]) || !std::isfinite(aabb[4]) || !std::isfinite(aabb[5])) {
@@ -270,6 +287,7 @@ omerf_status omerf_occupancy_grid(const float aabb[6], const float* occ, int32_t
   const float hz = (aabb[5] - aabb[4]) / (float)N[2];
   const long long blocks = (words + 255) / 256;
   if (blocks > 0x7fffffffLL) { set_error("occupancy grid too large"); return OMERF_ESHAPE; }
+  OMERF_LAUNCH_FAULT();
   occupancy_grid_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
       reinterpret_cast<const float2*>(occ), M, N[0], N[1], N[2], aabb[4], hz, bits, count);
   cudaError_t e = cudaGetLastError();
@@ -279,7 +297,12 @@ omerf_status omerf_occupancy_grid(const float aabb[6], const float* occ, int32_t
 omerf_status omerf_extract_bricks(const int32_t grid_res[3], int32_t brick, const int32_t* table, int32_t n_bricks,
                                   const void* src, const int32_t* src_table, int32_t src_n_bricks, int32_t feat_dtype,
                                   void* pool, void* stream) {
+  OMERF_API_RANGE();
   if (!grid_res || !table || !src || !pool) { set_error("NULL argument"); return OMERF_EINVAL; }
+  // a bounded wait of an earlier extraction that ran out is reported here
+  // (if omerf_sync has not reported it already)
+  omerf_status prev = take_device_error();
+  if (prev != OMERF_OK) return prev;
   if (brick < 2 || brick > 32 || (brick & (brick - 1))) { set_error("brick must be a power of two in 2..32"); return OMERF_EINVAL; }
   for (int a = 0; a < 3; a++)
     if (grid_res[a] < 2) { set_error("grid resolutions must be >= 2"); return OMERF_ESHAPE; }
@@ -314,12 +337,18 @@ omerf_status omerf_extract_bricks(const int32_t grid_res[3], int32_t brick, cons
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(extract_bricks_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       const int blocks = grid_for(entries, 1, 6 * sm_count());
+      // OMERF_FAULT=extract_wait: every CTA's first wait gives up at once
+      // (the load still completes and is waited for), for tests of the report
+      const int tries = fault_injected("extract_wait") ? 0 : (1 << 20);
+      OMERF_LAUNCH_FAULT();
       extract_bricks_tma_kernel<<<blocks, 32, smem, (cudaStream_t)stream>>>(
-          map, nb[0], nb[1], nb[2], brick, table, n_bricks, static_cast<unsigned char*>(pool), (unsigned)brick_bytes);
+          map, nb[0], nb[1], nb[2], brick, table, n_bricks, static_cast<unsigned char*>(pool), (unsigned)brick_bytes,
+          tries, device_error_word());
       cudaError_t e = cudaGetLastError();
       return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "brick extraction launch");
     }
   }
+  OMERF_LAUNCH_FAULT();
   const int blocks = grid_for(entries, 1, 16 * sm_count());
   extract_bricks_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(
       grid_res[0], grid_res[1], grid_res[2], brick, nb[0], nb[1], nb[2], table, n_bricks,
@@ -332,6 +361,7 @@ int32_t omerf_tma_available(void) { return tensor_map_encoder() != nullptr ? 1 :
 
 omerf_status omerf_plane_crop_rows(const float plane_z[2], int32_t Rz, const float* occ, int32_t M, int32_t* rows,
                                    float* z_range, void* stream) {
+  OMERF_API_RANGE();
   if (!plane_z || !occ || !rows || !z_range) { set_error("NULL argument"); return OMERF_EINVAL; }
   if (Rz < 2 || M < 1) { set_error("Rz must be >= 2 and M >= 1"); return OMERF_ESHAPE; }
   if (!(plane_z[0] < plane_z[1]) || !std::isfinite(plane_z[0]) || !std::isfinite(plane_z[1])) {
@@ -339,6 +369,7 @@ omerf_status omerf_plane_crop_rows(const float plane_z[2], int32_t Rz, const flo
     return OMERF_EINVAL;
   }
   if (!aligned(occ, 8) || !aligned(rows, 4) || !aligned(z_range, 4)) { set_error("misaligned argument"); return OMERF_EINVAL; }
+  OMERF_LAUNCH_FAULT();
   plane_crop_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float2*>(occ), (long long)M * M,
                                                           plane_z[0], plane_z[1], Rz, rows, z_range);
   cudaError_t e = cudaGetLastError();
@@ -347,6 +378,7 @@ omerf_status omerf_plane_crop_rows(const float plane_z[2], int32_t Rz, const flo
 
 omerf_status omerf_crop_planes(const void* src, int64_t n_outer, int32_t Rz, int32_t k0, int32_t k1,
                                int32_t feat_dtype, void* dst, void* stream) {
+  OMERF_API_RANGE();
   if (!src || !dst) { set_error("NULL argument"); return OMERF_EINVAL; }
   if (n_outer < 1 || Rz < 2 || k0 < 0 || k1 <= k0 || k1 > Rz - 1) {
     set_error("need n_outer >= 1 and 0 <= k0 < k1 <= Rz - 1");
@@ -356,6 +388,7 @@ omerf_status omerf_crop_planes(const void* src, int64_t n_outer, int32_t Rz, int
   if (!aligned(src, 16) || !aligned(dst, 16)) { set_error("planes must be 16-byte aligned"); return OMERF_EINVAL; }
   const int words = feat_dtype == OMERF_F32 ? 2 : 1;
   const long long total = (long long)n_outer * (k1 - k0 + 1) * words;
+  OMERF_LAUNCH_FAULT();
   crop_rows_kernel<<<grid_for(total, 256, 8 * sm_count()), 256, 0, (cudaStream_t)stream>>>(
       static_cast<const uint4*>(src), (long long)n_outer, Rz, k0, k1 - k0 + 1, words, static_cast<uint4*>(dst));
   cudaError_t e = cudaGetLastError();

@@ -20,7 +20,7 @@ namespace omerf {
 constexpr size_t kNoAllocCounterBytes = kCounterSlots * sizeof(unsigned);
 constexpr size_t kNoAllocHullOffset = kNoAllocCounterBytes;
 constexpr size_t kNoAllocCoarseOffset = kNoAllocHullOffset + 256;
-constexpr size_t kNoAllocScratchBytes = 1u << 20;  // 1 MiB
+constexpr size_t kNoAllocScratchBytes = 8u << 20;  // 8 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -56,6 +56,7 @@ using namespace omerf;
 
 extern "C" omerf_status omerf_render_noalloc(const omerf_scene_desc* desc, const omerf_camera* cam, const float* rays,
                                              int64_t n, float* rgb, int32_t* count, void* stream) {
+  OMERF_API_RANGE();
   omerf_status st = validate_desc(desc);
   if (st != OMERF_OK) return st;
   if (!rgb && n > 0) {
@@ -74,6 +75,21 @@ extern "C" omerf_status omerf_render_noalloc(const omerf_scene_desc* desc, const
     set_error("rays is NULL and no camera given");
     return OMERF_EINVAL;
   }
+  // The same pointer checks as omerf_scene_create and omerf_render (none of
+  // them allocates): the description's arrays must be device memory, and the
+  // outputs device or page-locked host memory, written through its device alias.
+  const void* ptrs[] = {desc->grid, desc->brick_table, desc->plane_xy, desc->plane_xz, desc->plane_yz, desc->occ,
+                        desc->mlp};
+  const char* names[] = {"grid", "brick_table", "plane_xy", "plane_xz", "plane_yz", "occ", "mlp"};
+  for (int i = 0; i < 7; i++)
+    if ((st = check_device_ptr(ptrs[i], names[i])) != OMERF_OK) return st;
+  if (n > 0) {
+    void *rd = nullptr, *cd = nullptr;
+    if ((st = output_ptr(rgb, &rd, "rgb")) != OMERF_OK) return st;
+    if ((st = output_ptr(count, &cd, "count")) != OMERF_OK) return st;
+    rgb = static_cast<float*>(rd);
+    count = static_cast<int32_t*>(cd);
+  }
   // A scene on the stack: the same description and geometry as a handle,
   // with its device state placed in the static scratch array.
   omerf_scene s;
@@ -82,12 +98,11 @@ extern "C" omerf_status omerf_render_noalloc(const omerf_scene_desc* desc, const
   const size_t cells = (size_t)s.Mc * (size_t)s.Mc;
   const size_t coarse_bytes = (cells * sizeof(float2) + 255) / 256 * 256;
   const size_t nbr_offset = kNoAllocCoarseOffset + coarse_bytes;
-  const size_t nbr_bytes = desc->brick ? (size_t)desc->n_bricks * 8 * sizeof(int) : 0;
+  const size_t nbr_bytes = brick_records_bytes(desc);
   if (nbr_offset + nbr_bytes > kNoAllocScratchBytes) {
-    set_error("a %d x %d occupancy plane (%zu-byte coarse grid) with %d bricks (%zu bytes of neighbour records) needs "
+    set_error("a %d x %d occupancy plane (%zu-byte coarse grid) with %zu bytes of brick neighbour records needs "
               "more than the %zu bytes the no-allocation render reserves",
-              desc->occ_res, desc->occ_res, coarse_bytes, desc->brick ? desc->n_bricks : 0, nbr_bytes,
-              kNoAllocScratchBytes - kNoAllocCoarseOffset);
+              desc->occ_res, desc->occ_res, coarse_bytes, nbr_bytes, kNoAllocScratchBytes - kNoAllocCoarseOffset);
     return OMERF_ESHAPE;
   }
   cudaError_t e = cudaGetDevice(&s.device);
@@ -111,6 +126,7 @@ extern "C" omerf_status omerf_render_noalloc(const omerf_scene_desc* desc, const
   // is zeroed by the launch.
   cudaStream_t cs = (cudaStream_t)stream;
   const long occ_cells = (long)desc->occ_res * desc->occ_res;
+  OMERF_LAUNCH_FAULT();
   hull_kernel<<<1, 1024, 0, cs>>>(s.geo.occ, occ_cells, s.state);
   coarse_hull_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, cs>>>(s.geo.occ, desc->occ_res, s.clog2, s.Mc,
                                                                       s.chull);

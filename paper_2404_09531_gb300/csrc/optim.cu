@@ -50,6 +50,7 @@ extern "C" {
 
 omerf_status omerf_adam_step(const omerf_adam_group* groups, int32_t n_groups, float beta1, float beta2, float eps,
                              int64_t step, void* stream) {
+  OMERF_API_RANGE();
   if (!groups || n_groups < 1 || n_groups > kMaxGroups) {
     set_error("n_groups must be in 1..%d", kMaxGroups);
     return OMERF_EINVAL;
@@ -88,6 +89,7 @@ omerf_status omerf_adam_step(const omerf_adam_group* groups, int32_t n_groups, f
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long want = (total + 255) / 256;
   const int grid = (int)(want < 8L * sms ? want : 8L * sms);
+  OMERF_LAUNCH_FAULT();
   adam_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "adam kernel");

@@ -248,6 +248,7 @@ int reg_grid(K kern, long units_per_block, long n, int num_sms) {
 omerf_status omerf_sparsity_loss(const omerf_scene* s, const float* points, int64_t n, float lambda,
                                  const float* grad_scale, float* loss, float* g_grid, float* g_xy, float* g_xz,
                                  float* g_yz, void* stream) {
+  OMERF_API_RANGE();
   const float* gp[4] = {g_grid, g_xy, g_xz, g_yz};
   omerf_status st = check_reg_args(s, points, n, lambda, loss, gp, 4, nullptr);
   if (st != OMERF_OK) return st;
@@ -258,6 +259,7 @@ omerf_status omerf_sparsity_loss(const omerf_scene* s, const float* points, int6
   const bool bf16 = s->desc.feat_dtype == OMERF_BF16, sparse = s->desc.brick > 0;
   auto k = bf16 ? (sparse ? sparsity_kernel<__nv_bfloat16, true> : sparsity_kernel<__nv_bfloat16, false>)
                 : (sparse ? sparsity_kernel<float, true> : sparsity_kernel<float, false>);
+  OMERF_LAUNCH_FAULT();
   k<<<reg_grid(k, kThreads, n, s->num_sms), kThreads, 0, cs>>>(s->geo, points, n, lam_n, grad_scale, loss, G);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "sparsity loss launch");
@@ -266,6 +268,7 @@ omerf_status omerf_sparsity_loss(const omerf_scene* s, const float* points, int6
 omerf_status omerf_entropy_loss(const omerf_scene* s, const float* rays, int64_t n, float lambda,
                                 const float* grad_scale, float* loss, float* g_grid, float* g_xy, float* g_xz,
                                 float* g_yz, float* g_occ, void* stream) {
+  OMERF_API_RANGE();
   const float* gp[4] = {g_grid, g_xy, g_xz, g_yz};
   omerf_status st = check_reg_args(s, rays, n, lambda, loss, gp, 4, g_occ);
   if (st != OMERF_OK) return st;
@@ -277,6 +280,7 @@ omerf_status omerf_entropy_loss(const omerf_scene* s, const float* rays, int64_t
   const bool bf16 = s->desc.feat_dtype == OMERF_BF16, sparse = s->desc.brick > 0;
   auto k = bf16 ? (sparse ? entropy_kernel<__nv_bfloat16, true> : entropy_kernel<__nv_bfloat16, false>)
                 : (sparse ? entropy_kernel<float, true> : entropy_kernel<float, false>);
+  OMERF_LAUNCH_FAULT();
   k<<<reg_grid(k, rays_per_block, n, s->num_sms), kThreads, 0, cs>>>(s->geo, rays, n, lam_n, grad_scale, loss, G);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "entropy loss launch");

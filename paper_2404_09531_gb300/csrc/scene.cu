@@ -92,6 +92,8 @@ struct BrickArgs {
   int L[3], B, M, nb[3];
   const float2* occ;
   int* table;
+  const int* old_table;  // growing: bricks already stored are kept (NULL otherwise)
+  int* missing;          // growing: count of bricks the rule adds
 };
 
 __global__ void brick_flag_kernel(const BrickArgs a, long total) {
@@ -117,25 +119,36 @@ __global__ void brick_flag_kernel(const BrickArgs a, long total) {
       const float2 z = a.occ[i * a.M + j];
       if (z.x <= z.y && z.y >= zlo && z.x <= zhi) hit = 1;
     }
+  if (a.old_table) {
+    const int kept = a.old_table[id] >= 0;
+    if (hit && !kept) atomicAdd(a.missing, 1);
+    hit |= kept;
+  }
   a.table[id] = hit;
 }
 
-// Neighbour records of a brick grid: for each allocated brick b at brick
-// coordinates (bi, bj, bk), nbr[b][dx*4 + dy*2 + dz] is the pool index of the
-// brick at (bi + dx, bj + dy, bk + dz), -1 if unallocated or outside.
+// Neighbour records of a brick grid, one per brick of the grid (stored or
+// not): nbr[id][dx*4 + dy*2 + dz] is the pool index of the brick at
+// (bi + dx, bj + dy, bk + dz), -1 if it is not stored or outside the grid
+// (slot 0 is the brick's own table entry).  A sample whose cell reaches
+// into neighbour bricks finds the brick of each of its 8 corners in the
+// record of its lowest corner's brick, with one 256-bit load.
 __global__ void brick_neighbor_kernel(const int* __restrict__ table, int nbx, int nby, int nbz, int n_bricks,
                                       int* __restrict__ nbr) {
   const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (long)nbx * nby * nbz) return;
-  const int b = table[id];
-  if (b < 0 || b >= n_bricks) return;
   const int bk = (int)(id % nbz), bj = (int)((id / nbz) % nby), bi = (int)(id / ((long)nbz * nby));
+  int v[8];
+#pragma unroll
   for (int c = 0; c < 8; c++) {
     const int x = bi + ((c >> 2) & 1), y = bj + ((c >> 1) & 1), z = bk + (c & 1);
-    int v = -1;
-    if (x < nbx && y < nby && z < nbz) v = table[((long)x * nby + y) * nbz + z];
-    nbr[8l * b + c] = v;
+    int b = -1;
+    if (x < nbx && y < nby && z < nbz) b = table[((long)x * nby + y) * nbz + z];
+    v[c] = (b >= 0 && b < n_bricks) ? b : -1;
   }
+  int4* out = reinterpret_cast<int4*>(nbr + 8l * id);
+  out[0] = make_int4(v[0], v[1], v[2], v[3]);
+  out[1] = make_int4(v[4], v[5], v[6], v[7]);
 }
 
 // Count brick-table entries that are neither -1 nor a pool index.
@@ -288,7 +301,7 @@ omerf_status validate_desc(const omerf_scene_desc* d) {
   return OMERF_OK;
 }
 
-static omerf_status check_device_ptr(const void* p, const char* name) {
+omerf_status check_device_ptr(const void* p, const char* name) {
   if (!p) return OMERF_OK;
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, p);
@@ -350,16 +363,21 @@ void fill_geo(omerf_scene* s) {
   g.Mc = s->Mc;
 }
 
+size_t brick_records_bytes(const omerf_scene_desc* d) {
+  if (!d->brick) return 0;
+  size_t n = 8 * sizeof(int);
+  for (int a = 0; a < 3; a++) n *= (size_t)((d->grid_res[a] + d->brick - 1) / d->brick);
+  return n;
+}
+
 omerf_status build_brick_neighbors(omerf_scene* s, cudaStream_t stream) {
   const Geo& g = s->geo;
   const long total = (long)g.nb[0] * g.nb[1] * g.nb[2];
-  cudaError_t e = cudaMemsetAsync(s->nbr, 0xff, (size_t)s->desc.n_bricks * 8 * sizeof(int), stream);
-  if (e != cudaSuccess) return cuda_fail(e, "neighbour table memset");
   if (total > 0)
     brick_neighbor_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(s->desc.brick_table, g.nb[0], g.nb[1],
                                                                               g.nb[2], s->desc.n_bricks, s->nbr);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "neighbour table kernel");
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "neighbour record kernel");
 }
 
 // Coarse level: the smallest power-of-two block of occupancy cells whose side
@@ -396,12 +414,33 @@ Cam to_cam(const omerf_camera* c) {
   return k;
 }
 
+// An output buffer of the render: device memory, or page-locked host memory
+// the device addresses directly (the pointer the device uses is returned).
+omerf_status output_ptr(void* p, void** dev, const char* name) {
+  *dev = p;
+  if (!p) return OMERF_OK;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("%s: not a CUDA-accessible pointer", name);
+    return OMERF_EDEVICE;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return OMERF_OK;
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *dev = at.devicePointer;
+    return OMERF_OK;
+  }
+  set_error("%s must be device memory or page-locked host memory", name);
+  return OMERF_EDEVICE;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
 
 omerf_status omerf_scene_create(const omerf_scene_desc* desc, void* stream, omerf_scene** out) {
+  OMERF_API_RANGE();
   if (!out) { set_error("out is NULL"); return OMERF_EINVAL; }
   *out = nullptr;
   omerf_status st = validate_desc(desc);
@@ -419,15 +458,15 @@ omerf_status omerf_scene_create(const omerf_scene_desc* desc, void* stream, omer
   s->device = dev;
   cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (s->num_sms < 1) s->num_sms = 1;
-  e = cudaMalloc(&s->state, 64 * sizeof(float));
+  // OMERF_FAULT=alloc: the handle's first allocation fails (tests of the path)
+  e = fault_injected("alloc") ? cudaErrorMemoryAllocation : cudaMalloc(&s->state, 64 * sizeof(float));
   if (e != cudaSuccess) { cudaGetLastError(); delete s; set_error("cudaMalloc: %s", cudaGetErrorString(e)); return OMERF_ENOMEM; }
   e = cudaMalloc(&s->counters, kCounterSlots * sizeof(unsigned));
   if (e != cudaSuccess) { cudaGetLastError(); cudaFree(s->state); delete s; set_error("cudaMalloc: %s", cudaGetErrorString(e)); return OMERF_ENOMEM; }
   choose_coarse_level(s);
   e = cudaMalloc(&s->chull, (size_t)s->Mc * s->Mc * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&s->cams, kMaxCams * sizeof(CamRec));
-  if (e == cudaSuccess && desc->brick && desc->n_bricks > 0)
-    e = cudaMalloc(&s->nbr, (size_t)desc->n_bricks * 8 * sizeof(int));
+  if (e == cudaSuccess && desc->brick) e = cudaMalloc(&s->nbr, brick_records_bytes(desc));
   if (e != cudaSuccess) {
     cudaGetLastError();
     omerf_scene_destroy(s);
@@ -458,7 +497,7 @@ omerf_status omerf_scene_create(const omerf_scene_desc* desc, void* stream, omer
       set_error("the brick table holds %u entries outside [-1, n_bricks = %d)", nbad, desc->n_bricks);
       return OMERF_ESHAPE;
     }
-    if (desc->n_bricks > 0 && (st = build_brick_neighbors(s, cs)) != OMERF_OK) {
+    if ((st = build_brick_neighbors(s, cs)) != OMERF_OK) {
       omerf_scene_destroy(s);
       return st;
     }
@@ -470,8 +509,10 @@ omerf_status omerf_scene_create(const omerf_scene_desc* desc, void* stream, omer
 }
 
 omerf_status omerf_scene_update(omerf_scene* s, void* stream) {
+  OMERF_API_RANGE();
   if (!s) { set_error("scene is NULL"); return OMERF_EINVAL; }
   const long cells = (long)s->desc.occ_res * s->desc.occ_res;
+  OMERF_LAUNCH_FAULT();
   hull_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(s->geo.occ, cells, s->state);
   const int nc = s->Mc * s->Mc;
   coarse_hull_kernel<<<(nc + 255) / 256, 256, 0, (cudaStream_t)stream>>>(s->geo.occ, s->desc.occ_res, s->clog2,
@@ -481,6 +522,7 @@ omerf_status omerf_scene_update(omerf_scene* s, void* stream) {
 }
 
 void omerf_scene_destroy(omerf_scene* s) {
+  OMERF_API_RANGE();
   if (!s) return;
   cudaFree(s->state);
   cudaFree(s->counters);
@@ -490,8 +532,10 @@ void omerf_scene_destroy(omerf_scene* s) {
   delete s;
 }
 
-omerf_status omerf_build_brick_table(const float aabb[6], const int32_t grid_res[3], int32_t brick, const float* occ,
-                                     int32_t occ_res, int32_t* table, int32_t* n_alloc, void* stream) {
+// Shared by omerf_build_brick_table and omerf_grow_brick_table.
+static omerf_status brick_table_impl(const float aabb[6], const int32_t grid_res[3], int32_t brick, const float* occ,
+                                     int32_t occ_res, const int32_t* old_table, int32_t* table, int32_t* n_alloc,
+                                     int32_t* missing, void* stream, const char* entry) {
   if (!aabb || !grid_res || !occ || !table || !n_alloc) { set_error("NULL argument"); return OMERF_EINVAL; }
   if (brick < 2 || brick > 32 || (brick & (brick - 1))) { set_error("brick must be a power of two in 2..32"); return OMERF_EINVAL; }
   if (occ_res < 1) { set_error("occ_res must be >= 1"); return OMERF_ESHAPE; }
@@ -511,17 +555,40 @@ omerf_status omerf_build_brick_table(const float aabb[6], const int32_t grid_res
   }
   a.occ = reinterpret_cast<const float2*>(occ);
   a.table = table;
+  a.old_table = old_table;
+  a.missing = missing;
   const long total = (long)a.nb[0] * a.nb[1] * a.nb[2];
   if (total > (1l << 31)) { set_error("too many bricks"); return OMERF_ESHAPE; }
   cudaStream_t s = (cudaStream_t)stream;
+  if (fault_injected("launch")) return injected_launch_failure(entry);
+  if (missing) {
+    cudaError_t e = cudaMemsetAsync(missing, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e, "brick table memset");
+  }
   brick_flag_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(a, total);
   brick_scan_kernel<<<1, 1024, 0, s>>>(table, total, n_alloc);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "brick table kernels");
 }
 
+omerf_status omerf_build_brick_table(const float aabb[6], const int32_t grid_res[3], int32_t brick, const float* occ,
+                                     int32_t occ_res, int32_t* table, int32_t* n_alloc, void* stream) {
+  OMERF_API_RANGE();
+  return brick_table_impl(aabb, grid_res, brick, occ, occ_res, nullptr, table, n_alloc, nullptr, stream, __func__);
+}
+
+omerf_status omerf_grow_brick_table(const float aabb[6], const int32_t grid_res[3], int32_t brick, const float* occ,
+                                    int32_t occ_res, const int32_t* old_table, int32_t* table, int32_t* n_alloc,
+                                    int32_t* missing, void* stream) {
+  OMERF_API_RANGE();
+  if (!old_table || !missing) { set_error("NULL argument"); return OMERF_EINVAL; }
+  if (old_table == table) { set_error("table must not be old_table"); return OMERF_EINVAL; }
+  return brick_table_impl(aabb, grid_res, brick, occ, occ_res, old_table, table, n_alloc, missing, stream, __func__);
+}
+
 omerf_status omerf_ray_interval(const omerf_scene* s, const omerf_camera* cam, const float* rays, int64_t n,
                                 int32_t* k_range, void* stream) {
+  OMERF_API_RANGE();
   if (!s || (!k_range && n > 0)) { set_error("NULL argument"); return OMERF_EINVAL; }
   if (n < 0) { set_error("n must be >= 0"); return OMERF_ESHAPE; }
   omerf_status st;
@@ -534,34 +601,16 @@ omerf_status omerf_ray_interval(const omerf_scene* s, const omerf_camera* cam, c
     return OMERF_EINVAL;
   }
   if (n == 0) return OMERF_OK;
+  OMERF_LAUNCH_FAULT();
   interval_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(s->geo, k, cam ? 1 : 0, rays, n,
                                                                                   reinterpret_cast<int2*>(k_range));
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "interval kernel");
 }
 
-// An output buffer of the render: device memory, or page-locked host memory
-// the device addresses directly (the pointer the device uses is returned).
-static omerf_status output_ptr(void* p, void** dev, const char* name) {
-  *dev = p;
-  if (!p) return OMERF_OK;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("%s: not a CUDA-accessible pointer", name);
-    return OMERF_EDEVICE;
-  }
-  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return OMERF_OK;
-  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
-    *dev = at.devicePointer;
-    return OMERF_OK;
-  }
-  set_error("%s must be device memory or page-locked host memory", name);
-  return OMERF_EDEVICE;
-}
-
 omerf_status omerf_render(const omerf_scene* s, const omerf_camera* cam, const float* rays, int64_t n, float* rgb,
                           int32_t* count, void* stream) {
+  OMERF_API_RANGE();
   if (!s || (!rgb && n > 0)) { set_error("NULL argument"); return OMERF_EINVAL; }
   if (n < 0) { set_error("n must be >= 0"); return OMERF_ESHAPE; }
   omerf_status st;
@@ -581,6 +630,7 @@ omerf_status omerf_render(const omerf_scene* s, const omerf_camera* cam, const f
     return OMERF_EINVAL;
   }
   if (n == 0) return OMERF_OK;
+  OMERF_LAUNCH_FAULT();
   cudaError_t e = launch_march_fwd(s, cam ? &k : nullptr, rays, n, rgb, count, nullptr, nullptr, 0, nullptr,
                                    nullptr, nullptr, (cudaStream_t)stream);
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "render launch");
@@ -588,6 +638,7 @@ omerf_status omerf_render(const omerf_scene* s, const omerf_camera* cam, const f
 
 omerf_status omerf_render_cameras(const omerf_scene* s, const omerf_camera* cams, int32_t n_cams, float* rgb,
                                   int32_t* count, void* stream) {
+  OMERF_API_RANGE();
   if (!s || (!cams && n_cams > 0)) { set_error("NULL argument"); return OMERF_EINVAL; }
   if (n_cams < 0) { set_error("n_cams must be >= 0"); return OMERF_ESHAPE; }
   if (n_cams == 0) return OMERF_OK;
@@ -614,6 +665,7 @@ omerf_status omerf_render_cameras(const omerf_scene* s, const omerf_camera* cams
       supers += (long)rec[c].super_x * ((k.height + 15) / 16);
       rays += (long)k.width * k.height;
     }
+    OMERF_LAUNCH_FAULT();
     // pageable source: the copy is staged before the call returns
     cudaError_t e = cudaMemcpyAsync(s->cams, rec, m * sizeof(CamRec), cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "camera upload");
@@ -642,9 +694,11 @@ static omerf_status check_train_args(const omerf_scene* s, const float* rays, co
 
 omerf_status omerf_train_fwd(const omerf_scene* s, const float* rays, const float* target, const float* smooth_dirs,
                              int64_t n, int32_t K, const float lambda[3], void* saved, float* loss, void* stream) {
+  OMERF_API_RANGE();
   omerf_status st = check_train_args(s, rays, target, smooth_dirs, n, K, lambda, saved);
   if (st != OMERF_OK) return st;
   if (!loss) { set_error("loss is NULL"); return OMERF_EINVAL; }
+  OMERF_LAUNCH_FAULT();
   cudaStream_t cs = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(loss, 0, 4 * sizeof(float), cs);
   if (e != cudaSuccess) return cuda_fail(e, "loss memset");
@@ -664,12 +718,14 @@ omerf_status omerf_train_bwd(const omerf_scene* s, const float* rays, const floa
                              int64_t n, int32_t K, const float lambda[3], void* saved, const float* grad_scale,
                              float* g_grid, float* g_xy, float* g_xz, float* g_yz, float* g_occ, float* g_mlp,
                              void* stream) {
+  OMERF_API_RANGE();
   omerf_status st = check_train_args(s, rays, target, smooth_dirs, n, K, lambda, saved);
   if (st != OMERF_OK) return st;
   const void* gps[] = {g_grid, g_xy, g_xz, g_yz};
   for (const void* p : gps)
     if (p && !aligned(p, 16)) { set_error("gradient buffers must be 16-byte aligned"); return OMERF_EINVAL; }
   if (g_occ && !aligned(g_occ, 8)) { set_error("g_occ must be 8-byte aligned"); return OMERF_EINVAL; }
+  OMERF_LAUNCH_FAULT();
   cudaStream_t cs = (cudaStream_t)stream;
   cudaError_t e;
   if (n > 0) {
@@ -690,6 +746,7 @@ omerf_status omerf_train_bwd(const omerf_scene* s, const float* rays, const floa
 omerf_status omerf_train_step(const omerf_scene* s, const float* rays, const float* target, const float* smooth_dirs,
                               int64_t n, int32_t K, const float lambda[3], void* saved, float* loss, float* g_grid,
                               float* g_xy, float* g_xz, float* g_yz, float* g_occ, float* g_mlp, void* stream) {
+  OMERF_API_RANGE();
   // The forward only marches and saves the per-ray state; the MLP backward,
   // which evaluates the deferred MLP anyway, adds the Charbonnier and
   // smoothness terms to the loss, and one L_occ launch adds its loss and
@@ -701,6 +758,7 @@ omerf_status omerf_train_step(const omerf_scene* s, const float* rays, const flo
   for (const void* p : gps)
     if (p && !aligned(p, 16)) { set_error("gradient buffers must be 16-byte aligned"); return OMERF_EINVAL; }
   if (g_occ && !aligned(g_occ, 8)) { set_error("g_occ must be 8-byte aligned"); return OMERF_EINVAL; }
+  OMERF_LAUNCH_FAULT();
   cudaStream_t cs = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(loss, 0, 4 * sizeof(float), cs);
   if (e != cudaSuccess) return cuda_fail(e, "loss memset");
@@ -720,11 +778,12 @@ omerf_status omerf_train_step(const omerf_scene* s, const float* rays, const flo
 }
 
 omerf_status omerf_sync(void* stream, int32_t timeout_ms) {
+  OMERF_API_RANGE();
   cudaStream_t cs = (cudaStream_t)stream;
   auto t0 = std::chrono::steady_clock::now();
   for (;;) {
     cudaError_t e = cudaStreamQuery(cs);
-    if (e == cudaSuccess) return OMERF_OK;
+    if (e == cudaSuccess) return take_device_error();
     if (e != cudaErrorNotReady) return cuda_fail(e, "stream");
     if (timeout_ms >= 0) {
       auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();

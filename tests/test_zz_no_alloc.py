@@ -83,3 +83,31 @@ def test_bf16_brick_scene_matches_the_regular_render():
     ref = om.render(scene, camera=cam)
     for call in range(2):
         _check_same(ref, om.render_noalloc(scene, camera=cam, count=torch.empty_like(ref[1])), f"bf16 call {call}")
+
+
+def test_output_pointers_are_checked_like_the_regular_render():
+    """A pageable host buffer is rejected with OMERF_EDEVICE before any launch
+    (as omerf_render rejects it); page-locked host buffers are written
+    through their device alias and match the regular render."""
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    cam = synth.make_cameras(1)[0]
+    n = cam["width"] * cam["height"]
+    ref = om.render(scene, camera=cam)
+    lib = om.lib()
+    cs = binding.camera_struct(cam)
+    pageable = np.zeros((n, 3), np.float32)
+    rc = lib.omerf_render_noalloc(ctypes.byref(scene._desc), ctypes.byref(cs), None, n,
+                                  ctypes.c_void_p(pageable.ctypes.data), None, None)
+    assert rc == -3
+    assert b"rgb" in lib.omerf_last_error()
+    assert not pageable.any()
+    pinned = torch.zeros((n, 3), dtype=torch.float32, pin_memory=True)
+    pinned_cnt = torch.zeros(n, dtype=torch.int32, pin_memory=True)
+    for call in range(2):
+        rc = lib.omerf_render_noalloc(ctypes.byref(scene._desc), ctypes.byref(cs), None, n,
+                                      ctypes.c_void_p(pinned.data_ptr()), ctypes.c_void_p(pinned_cnt.data_ptr()),
+                                      None)
+        assert rc == 0
+        torch.cuda.synchronize()
+        _check_same(ref, (pinned.cuda(), pinned_cnt.cuda()), f"page-locked output, call {call}")
