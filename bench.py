@@ -663,6 +663,34 @@ def run_native(args):
         tr_ms.append(a.elapsed_time(b))
     t_train = float(np.mean(tr_ms))
     loss = res["loss"].cpu().numpy().tolist()
+    dp_train = None
+    if ws > 1:
+        # ray-sharded data parallelism (weak scaling): a global batch of ws x
+        # 2^18 rays, each rank's shard its own 2^18 rays, one all-reduce of
+        # the gradients and loss inside the timed step
+        from paper_2404_09531_gb300 import data_parallel as dpm
+        g_rays = torch.cat([torch.as_tensor(synth.make_train_batch(3, 1 << 18, seed=3 + 7919 * r)["rays"])
+                            for r in range(ws)]).to(dev)
+        g_tgt = torch.cat([target] * ws)
+        g_dirs = torch.cat([dirs_d] * ws)
+        dstep = dpm.DataParallelStep({k: tuple(getattr(tscene, k).shape) for k in dpm.GRAD_KEYS}, dev)
+        for _ in range(args.warmup):
+            dstep(tscene, g_rays, g_tgt, g_dirs, lam, saved=saved)
+        dp_ms = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            import torch.distributed as dist
+            dist.barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dstep(tscene, g_rays, g_tgt, g_dirs, lam, saved=saved)
+            b.record(stream)
+            torch.cuda.synchronize()
+            dp_ms.append(a.elapsed_time(b))
+        t_dp = max_over_ranks(float(np.mean(dp_ms)), dev)
+        dp_train = {"value": ws * (1 << 18) / (t_dp * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": t_dp,
+                    "global_batch": ws * (1 << 18), "scaling": "weak",
+                    "note": "ray-sharded fwd+bwd, one NCCL all-reduce of gradients + loss per step, max over ranks"}
 
     # the full optimisation step of appendix A: fwd + bwd, fused Adam over
     # features, occupancy plane and MLP (one launch), hull update
@@ -762,6 +790,7 @@ def run_native(args):
                   "regularizers": {"sparsity_us": float(np.mean(sp_ms)) * 1e3, "points": 1 << 14,
                                    "entropy_us": float(np.mean(en_ms)) * 1e3, "rays": 1 << 10,
                                    "note": "Eqs. 13-14, loss + gradient, one launch each"},
+                  "data_parallel": dp_train,
                   "adam": {"us": t_adam * 1e3, "params": n_params,
                            "achieved_gbs": 28.0 * n_params / (t_adam * 1e-3) / 1e9,
                            "note": "28 B per parameter (read p, g, m, v; write p, m, v)"}},

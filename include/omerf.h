@@ -59,7 +59,8 @@ typedef enum {
     OMERF_EDEVICE = -3,  /* no usable CUDA device, or a pointer is not device memory */
     OMERF_ECUDA = -4,    /* a CUDA runtime call failed */
     OMERF_ETIMEOUT = -5, /* omerf_sync gave up waiting, or a bounded device-side wait ran out */
-    OMERF_ENOMEM = -6    /* the library could not allocate its own state */
+    OMERF_ENOMEM = -6,   /* the library could not allocate its own state */
+    OMERF_ECHECK = -7    /* the checking build counted feature reads outside the arrays */
 } omerf_status;
 
 enum { OMERF_F32 = 0, OMERF_BF16 = 1 };
@@ -416,6 +417,25 @@ omerf_status omerf_probe_load_bandwidth(const float *buf, int64_t bytes_per_cta,
  * after timeout_ms milliseconds (< 0 waits without limit), OMERF_ECUDA if
  * the stream reported an error. */
 omerf_status omerf_sync(void *stream, int32_t timeout_ms);
+
+/* ---- the checking build (libomerf_check.so) ------------------------------
+ * The same sources compiled with OMERF_CHECK=1: every feature read of the
+ * march, the training backward and the regularisers is bounds-checked
+ * against the arrays' sizes (a read outside is counted and skipped, its
+ * gradient write too), and every corner read of a brick the table does not
+ * store (read as zero, Eq. 2 with Sec. 4.4's sparse storage) is counted.  A
+ * table built by omerf_build_brick_table never causes one for an evaluated
+ * sample; both counts are 0 on valid inputs.  The default build has neither
+ * check and no counter. */
+
+/* 1 in the checking build, 0 otherwise.  Host-only. */
+int32_t omerf_check_build(void);
+
+/* The scene's counters since creation or the last reset: counts[0] corner
+ * reads of unstored bricks, counts[1] reads outside a feature array.  Waits
+ * for `stream`; reset != 0 zeroes them afterwards (on `stream`).  Returns
+ * OMERF_ECHECK if counts[1] > 0, OMERF_EINVAL in the default build (counts 0). */
+omerf_status omerf_check_counts(const omerf_scene *scene, uint64_t counts[2], int32_t reset, void *stream);
 
 /* Thread-local description of the last failure in this thread. */
 const char *omerf_last_error(void);

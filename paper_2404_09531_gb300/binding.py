@@ -8,7 +8,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libomerf.so")
+# OMERF_CHECK=1 in the environment selects the checking build (bounds and
+# unstored-brick counters; see include/omerf.h)
+_LIB_PATH = os.path.join(_HERE, "libomerf_check.so" if os.environ.get("OMERF_CHECK") == "1" else "libomerf.so")
 _lib = None
 
 OMERF_F32 = 0
@@ -86,6 +88,8 @@ SIGNATURES = {
     "omerf_lr_exponential": (ctypes.c_float, [ctypes.c_float, ctypes.c_float, _L, _L]),
     "omerf_lambda_occ": (ctypes.c_float, [_L]),
     "omerf_probe_load_bandwidth": (ctypes.c_int, [_P, _L, _I, _I, _P, _P]),
+    "omerf_check_build": (ctypes.c_int32, []),
+    "omerf_check_counts": (ctypes.c_int, [_P, _P, _I, _P]),
     "omerf_sync": (ctypes.c_int, [_P, _I]),
     "omerf_last_error": (ctypes.c_char_p, []),
 }
@@ -457,12 +461,16 @@ def train_bwd(scene, saved, inputs, lam=(1.0, 1e-2, 0.0), grad_scale=None, grads
 
 
 def train_step(scene, rays, target, smooth_dirs=None, lam=(1.0, 1e-2, 0.0), grads=None, saved=None,
-               stream=None):
-    """One fused forward + backward: returns {"loss": [4] tensor, "grads": dict}."""
+               stream=None, loss=None):
+    """One fused forward + backward: returns {"loss": [4] tensor, "grads": dict}.
+    ``loss`` may be a caller's float32 [4] device tensor (overwritten)."""
     rays_t, target_t, dirs_t, n, K = _train_inputs(scene, rays, target, smooth_dirs)
     if saved is None:
         saved = torch.empty(max(n, 1) * saved_bytes_per_ray() // 4, dtype=torch.float32, device=scene.device)
-    loss = torch.empty(4, dtype=torch.float32, device=scene.device)
+    if loss is None:
+        loss = torch.empty(4, dtype=torch.float32, device=scene.device)
+    elif not loss.is_cuda or loss.dtype != torch.float32 or loss.numel() < 4 or not loss.is_contiguous():
+        raise OmerfError("loss must be a contiguous float32 CUDA tensor of 4 values")
     if grads is None:
         grads = zero_grads(scene)
     _check(lib().omerf_train_step(scene.handle, _ptr(rays_t), _ptr(target_t), _ptr(dirs_t), n, K, _lam(lam),
@@ -643,6 +651,15 @@ def probe_load_bandwidth(buf: torch.Tensor, bytes_per_cta: int, ctas: int, passe
     _check(lib().omerf_probe_load_bandwidth(_ptr(buf), int(bytes_per_cta), int(ctas), int(passes), _ptr(sink),
                                             _stream(stream)), "omerf_probe_load_bandwidth")
     return int(ctas) * int(bytes_per_cta) * int(passes)
+
+
+def check_counts(scene: Scene, reset=True, stream=None):
+    """The checking build's counters of a scene: (corner reads of unstored
+    bricks, feature reads outside the arrays).  Raises in the default build,
+    or (status -7) if a read fell outside an array."""
+    c = (ctypes.c_uint64 * 2)()
+    _check(lib().omerf_check_counts(scene.handle, c, int(bool(reset)), _stream(stream)), "omerf_check_counts")
+    return int(c[0]), int(c[1])
 
 
 def sync(stream=None, timeout_ms=-1):

@@ -12,6 +12,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#ifndef OMERF_CHECK
+#define OMERF_CHECK 0  // 1 in the checking build (libomerf_check.so): bounds and brick counters
+#endif
+
 namespace omerf {
 
 constexpr int kNch = 8;
@@ -50,6 +54,11 @@ struct Geo {
   // planes: texel offset of a z-range cropped to the occupancy bounds,
   // (z0' - z0) ps[2] (last, so that the fields above keep their offsets)
   float pzoff;
+  // elements of the grid (or pool) and of the XY, XZ, YZ planes, and the
+  // checking build's counters [2] (unallocated corner reads, reads outside
+  // an array); the default build reads neither
+  long long lim[4];
+  unsigned long long* check;
 };
 
 struct Cam {
@@ -251,6 +260,39 @@ struct Texel<__nv_bfloat16> {
   }
 };
 
+// Checking build: count the corners of a stencil whose brick is not stored
+// (they read as zero); the default build does nothing.
+__device__ __forceinline__ void check_unallocated(const Geo& g, const int off[8]) {
+#if OMERF_CHECK
+  int n = 0;
+#pragma unroll
+  for (int c = 0; c < 8; c++) n += off[c] < 0;
+  if (n && g.check) atomicAdd(g.check, (unsigned long long)n);
+#endif
+}
+
+// Checking build: whether the 8 channels at element offset off lie inside
+// feature array q (0 grid or pool, 1..3 the XY, XZ, YZ planes); a read
+// outside is counted and skipped.  The default build always reads.
+__device__ __forceinline__ bool check_range(const Geo& g, int q, int off) {
+#if OMERF_CHECK
+  if (off >= 0 && (long long)off + kNch <= g.lim[q]) return true;
+  if (g.check) atomicAdd(g.check + 1, 1ull);
+  return false;
+#else
+  return true;
+#endif
+}
+
+// The same test without counting (for writes at offsets already checked).
+__device__ __forceinline__ bool in_range(const Geo& g, int q, int off) {
+#if OMERF_CHECK
+  return off >= 0 && (long long)off + kNch <= g.lim[q];
+#else
+  return true;
+#endif
+}
+
 // Element offsets of the 8 grid corners (-1 for an unallocated brick) and
 // their trilinear weights, corner order (dx, dy, dz) with dz fastest.
 template <bool SPARSE>
@@ -300,6 +342,7 @@ __device__ __forceinline__ void grid_stencil(const Geo& g, const float p[3], int
       const int li = (i[0] + dx) & m, lj = (i[1] + dy) & m, lk = (i[2] + dz) & m;
       off[c] = b < 0 ? -1 : ((((b * B + li) * B + lj) * B) + lk) * kNch;
     }
+    check_unallocated(g, off);
   }
 }
 
@@ -340,7 +383,7 @@ __device__ __forceinline__ void gather_features(const Geo& g, const float p[3], 
 #pragma unroll
   for (int c = 0; c < 8; c++) {
     float v[8];
-    if (goff[c] >= 0) {
+    if (goff[c] >= 0 && check_range(g, 0, goff[c])) {
       Texel<FT>::load(g.grid, goff[c], v);
 #pragma unroll
       for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(gw[c], v[ch], t[ch]);
@@ -352,6 +395,7 @@ __device__ __forceinline__ void gather_features(const Geo& g, const float p[3], 
 #pragma unroll
     for (int c = 0; c < 4; c++) {
       float v[8];
+      if (!check_range(g, 1 + q, poff[4 * q + c])) continue;
       Texel<FT>::load(P, poff[4 * q + c], v);
 #pragma unroll
       for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(pw[4 * q + c], v[ch], t[ch]);

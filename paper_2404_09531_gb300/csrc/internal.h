@@ -14,6 +14,7 @@ struct omerf_scene {
   float2* chull = nullptr;         // device: coarse max-pooled occupancy grid [Mc][Mc]
   int* nbr = nullptr;              // device: brick neighbour records [nbx * nby * nbz][8] (brick grids)
   omerf::CamRec* cams = nullptr;   // device: camera records of a multi-camera render [kMaxCams]
+  unsigned long long* check = nullptr;  // device [2]: the checking build's counters (NULL otherwise)
   int clog2 = 0, Mc = 1;
   mutable std::atomic<unsigned> seq{0};
   int device = 0;

@@ -483,7 +483,7 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
       for (int c = 0; c < 8; c++) t[c] = 0.0f;
 #pragma unroll
       for (int c = 0; c < 8; c++) {
-        if (goff[c] < 0) continue;
+        if (goff[c] < 0 || !check_range(g, 0, goff[c])) continue;
         float v[8];
         Texel<FT>::load(g.grid, goff[c], v);
 #pragma unroll
@@ -494,6 +494,7 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
 #pragma unroll
         for (int c = 0; c < 4; c++) {
           float v[8];
+          if (!check_range(g, 1 + q, poff[4 * q + c])) continue;
           Texel<FT>::load(plane_base(g, q), poff[4 * q + c], v);
 #pragma unroll
           for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(pw[4 * q + c], v[ch], t[ch]);
@@ -562,7 +563,7 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
 #pragma unroll
             for (int ch = 0; ch < 8; ch++) v[ch] = fmaf(wn, dtn[j - 1][ch], v[ch]);
         }
-        if (act && emit && goff[c] >= 0) red8(a.g_grid, goff[c], v);
+        if (act && emit && goff[c] >= 0 && in_range(g, 0, goff[c])) red8(a.g_grid, goff[c], v);
       }
     }
     {
@@ -585,7 +586,7 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
 #pragma unroll
               for (int ch = 0; ch < 8; ch++) v[ch] = fmaf(wn, dtn[j - 1][ch], v[ch]);
           }
-          if (act && emit) red8(gp[q], poff[4 * q + c], v);
+          if (act && emit && in_range(g, 1 + q, poff[4 * q + c])) red8(gp[q], poff[4 * q + c], v);
         }
       }
     }

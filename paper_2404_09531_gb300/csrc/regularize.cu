@@ -46,12 +46,13 @@ __device__ __forceinline__ float density_at(const Geo& g, const float p[3], int 
   float t0 = 0.0f;
 #pragma unroll
   for (int c = 0; c < 8; c++)
-    if (goff[c] >= 0) t0 = fmaf(gw[c], load1(grid, goff[c]), t0);
+    if (goff[c] >= 0 && check_range(g, 0, goff[c])) t0 = fmaf(gw[c], load1(grid, goff[c]), t0);
 #pragma unroll
   for (int q = 0; q < 3; q++) {
     const FT* P = static_cast<const FT*>(plane_base(g, q));
 #pragma unroll
-    for (int c = 0; c < 4; c++) t0 = fmaf(pw[4 * q + c], load1(P, poff[4 * q + c]), t0);
+    for (int c = 0; c < 4; c++)
+      if (check_range(g, 1 + q, poff[4 * q + c])) t0 = fmaf(pw[4 * q + c], load1(P, poff[4 * q + c]), t0);
   }
   return t0;
 }
@@ -63,19 +64,20 @@ struct RegGrads {
 };
 
 // Scatter dL/dt_0 into channel 0 of the stencil's texels.
-__device__ __forceinline__ void scatter_density(const RegGrads& G, float dt0, const int goff[8], const float gw[8],
-                                                const int poff[12], const float pw[12]) {
+__device__ __forceinline__ void scatter_density(const Geo& g, const RegGrads& G, float dt0, const int goff[8],
+                                                const float gw[8], const int poff[12], const float pw[12]) {
   if (G.grid) {
 #pragma unroll
     for (int c = 0; c < 8; c++)
-      if (goff[c] >= 0 && gw[c] != 0.0f) atomicAdd(G.grid + goff[c], gw[c] * dt0);
+      if (goff[c] >= 0 && gw[c] != 0.0f && in_range(g, 0, goff[c])) atomicAdd(G.grid + goff[c], gw[c] * dt0);
   }
 #pragma unroll
   for (int q = 0; q < 3; q++) {
     if (!G.plane[q]) continue;
 #pragma unroll
     for (int c = 0; c < 4; c++)
-      if (pw[4 * q + c] != 0.0f) atomicAdd(G.plane[q] + poff[4 * q + c], pw[4 * q + c] * dt0);
+      if (pw[4 * q + c] != 0.0f && in_range(g, 1 + q, poff[4 * q + c]))
+        atomicAdd(G.plane[q] + poff[4 * q + c], pw[4 * q + c] * dt0);
   }
 }
 
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) sparsity_kernel(const Geo g, const f
     const float sigma = __expf(t0) * g.step;
     const float alpha = opacity_of(sigma);
     acc += alpha;
-    if (grads) scatter_density(G, c * (1.0f - alpha) * sigma, goff, gw, poff, pw);
+    if (grads) scatter_density(g, G, c * (1.0f - alpha) * sigma, goff, gw, poff, pw);
   }
   if (loss) block_add(lam_n * acc, loss);
 }
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kThreads) entropy_kernel(const Geo g, const fl
       const float a = Mv * alpha;
       if (!(a > 0.0f)) continue;
       const float da = -cS * (logf(a) - logS + L);
-      scatter_density(G, da * Mv * (1.0f - alpha) * sigma, goff, gw, poff, pw);
+      scatter_density(g, G, da * Mv * (1.0f - alpha) * sigma, goff, gw, poff, pw);
       if (G.occ && br != 0) {
         // M = r^2 on a ramp: dM/dz_min = -2 r / eps (lower), dM/dz_max = 2 r / eps (upper)
         const float dM = da * alpha * 2.0f * rr * g.inv_eps;

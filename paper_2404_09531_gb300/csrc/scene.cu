@@ -361,6 +361,12 @@ void fill_geo(omerf_scene* s) {
   g.nbr = s->nbr;
   g.clog2 = s->clog2;
   g.Mc = s->Mc;
+  const long long B3 = (long long)d.brick * d.brick * d.brick;
+  g.lim[0] = (d.brick ? (long long)d.n_bricks * B3 : (long long)d.grid_res[0] * d.grid_res[1] * d.grid_res[2]) * kNch;
+  g.lim[1] = (long long)d.plane_res[0] * d.plane_res[1] * kNch;
+  g.lim[2] = (long long)d.plane_res[0] * d.plane_res[2] * kNch;
+  g.lim[3] = (long long)d.plane_res[1] * d.plane_res[2] * kNch;
+  g.check = s->check;
 }
 
 size_t brick_records_bytes(const omerf_scene_desc* d) {
@@ -467,6 +473,10 @@ omerf_status omerf_scene_create(const omerf_scene_desc* desc, void* stream, omer
   e = cudaMalloc(&s->chull, (size_t)s->Mc * s->Mc * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&s->cams, kMaxCams * sizeof(CamRec));
   if (e == cudaSuccess && desc->brick) e = cudaMalloc(&s->nbr, brick_records_bytes(desc));
+  if (OMERF_CHECK && e == cudaSuccess) {
+    e = cudaMalloc(&s->check, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(s->check, 0, 2 * sizeof(unsigned long long));
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     omerf_scene_destroy(s);
@@ -529,6 +539,7 @@ void omerf_scene_destroy(omerf_scene* s) {
   cudaFree(s->chull);
   cudaFree(s->nbr);
   cudaFree(s->cams);
+  cudaFree(s->check);
   delete s;
 }
 
@@ -794,6 +805,28 @@ omerf_status omerf_sync(void* stream, int32_t timeout_ms) {
     }
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
+}
+
+int32_t omerf_check_build(void) { return OMERF_CHECK ? 1 : 0; }
+
+omerf_status omerf_check_counts(const omerf_scene* s, uint64_t counts[2], int32_t reset, void* stream) {
+  OMERF_API_RANGE();
+  if (!s || !counts) { set_error("NULL argument"); return OMERF_EINVAL; }
+  counts[0] = counts[1] = 0;
+  if (!s->check) { set_error("the library was built without OMERF_CHECK: nothing is counted"); return OMERF_EINVAL; }
+  cudaStream_t cs = (cudaStream_t)stream;
+  unsigned long long h[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(h, s->check, sizeof(h), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e == cudaSuccess && reset) e = cudaMemsetAsync(s->check, 0, sizeof(h), cs);
+  if (e != cudaSuccess) return cuda_fail(e, "check counters");
+  counts[0] = h[0];
+  counts[1] = h[1];
+  if (h[1]) {
+    set_error("%llu feature reads fell outside the arrays (skipped by the checking build)", h[1]);
+    return OMERF_ECHECK;
+  }
+  return OMERF_OK;
 }
 
 const char* omerf_last_error(void) { return g_err; }
