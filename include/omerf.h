@@ -99,7 +99,9 @@ typedef struct {
                                   the box's z-range */
 } omerf_scene_desc;
 
-/* Pinhole camera.  c2w is the 3x4 row-major camera-to-world matrix [R | o];
+/* Pinhole camera (host data, validated: finite pose and intrinsics, non-zero
+ * focal lengths and a non-singular R, else OMERF_EINVAL before any launch).
+ * c2w is the 3x4 row-major camera-to-world matrix [R | o];
  * the camera looks down its -z axis, image rows go along -y.  The ray of
  * pixel (px, py) has direction normalize(R (u, v, -1)) with
  * u = (px + 0.5 - cx) / fx and v = -(py + 0.5 - cy) / fy, evaluated in
@@ -179,10 +181,9 @@ omerf_status omerf_ray_interval(const omerf_scene *scene, const omerf_camera *ca
  *     w_i = T_i M_i alpha_i,  T_{i+1} = T_i (1 - M_i alpha_i),
  * and rgb = bg for a ray with no evaluated sample.
  *   cam    host camera (n == width * height, rays NULL), or NULL
- *   rays   device [n][6] float32 when cam is NULL: origin, unit direction,
- *          finite (device data is not validated on the host; a ray with a
- *          non-finite component evaluates no sample but may test up to
- *          2^24 lattice candidates, which is slow)
+ *   rays   device [n][6] float32 when cam is NULL: origin, unit direction
+ *          (device data is not validated on the host; a ray with a
+ *          non-finite component evaluates no sample and returns bg)
  *   rgb    float32 [n][3] (output): device memory, or page-locked host memory
  *          (cudaHostAlloc / cudaHostRegister), which the kernel writes
  *          directly (on Grace-Blackwell over the coherent chip-to-chip link),

@@ -104,6 +104,10 @@ __device__ __forceinline__ void camera_ray(const Cam& c, int px, int py, float o
 // sample positions, plus two lattice steps.  Returns false when empty.
 __device__ __forceinline__ bool lattice_range(const Geo& g, const float o[3], const float d[3], int& klo,
                                               int& khi) {
+  // a ray with a non-finite component evaluates no sample (every position
+  // test fails): skip its lattice scan
+  if (!(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]) && isfinite(d[0]) && isfinite(d[1]) && isfinite(d[2])))
+    return false;
   float tin = 0.0f, tout = __int_as_float(0x7f800000);
 #pragma unroll
   for (int a = 0; a < 3; a++) {

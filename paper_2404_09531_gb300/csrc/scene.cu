@@ -405,6 +405,15 @@ omerf_status validate_camera(const omerf_camera* c, int64_t n) {
   }
   if (c->width > (1 << 20) || c->height > (1 << 20)) { set_error("camera too large"); return OMERF_ESHAPE; }
   if (!(c->fx != 0.0f) || !(c->fy != 0.0f)) { set_error("camera focal lengths must be non-zero"); return OMERF_EINVAL; }
+  bool finite = std::isfinite(c->fx) && std::isfinite(c->fy) && std::isfinite(c->cx) && std::isfinite(c->cy);
+  for (int i = 0; i < 12; i++) finite = finite && std::isfinite(c->c2w[i]);
+  if (!finite) { set_error("camera pose and intrinsics must be finite"); return OMERF_EINVAL; }
+  // a pixel's direction R (u, v, -1) is zero-length only if R is singular
+  const float* m = c->c2w;
+  const double det = (double)m[0] * ((double)m[5] * m[10] - (double)m[6] * m[9]) -
+                     (double)m[1] * ((double)m[4] * m[10] - (double)m[6] * m[8]) +
+                     (double)m[2] * ((double)m[4] * m[9] - (double)m[5] * m[8]);
+  if (!(std::fabs(det) > 1e-12)) { set_error("camera rotation is singular: rays would have no direction"); return OMERF_EINVAL; }
   return OMERF_OK;
 }
 
@@ -625,13 +634,6 @@ omerf_status omerf_render(const omerf_scene* s, const omerf_camera* cam, const f
   if (!s || (!rgb && n > 0)) { set_error("NULL argument"); return OMERF_EINVAL; }
   if (n < 0) { set_error("n must be >= 0"); return OMERF_ESHAPE; }
   omerf_status st;
-  if (n > 0) {
-    void *rd = nullptr, *cd = nullptr;
-    if ((st = output_ptr(rgb, &rd, "rgb")) != OMERF_OK) return st;
-    if ((st = output_ptr(count, &cd, "count")) != OMERF_OK) return st;
-    rgb = static_cast<float*>(rd);
-    count = static_cast<int32_t*>(cd);
-  }
   Cam k{};
   if (cam) {
     if ((st = validate_camera(cam, n)) != OMERF_OK) return st;
@@ -639,6 +641,13 @@ omerf_status omerf_render(const omerf_scene* s, const omerf_camera* cam, const f
   } else if (!rays && n > 0) {
     set_error("rays is NULL and no camera given");
     return OMERF_EINVAL;
+  }
+  if (n > 0) {
+    void *rd = nullptr, *cd = nullptr;
+    if ((st = output_ptr(rgb, &rd, "rgb")) != OMERF_OK) return st;
+    if ((st = output_ptr(count, &cd, "count")) != OMERF_OK) return st;
+    rgb = static_cast<float*>(rd);
+    count = static_cast<int32_t*>(cd);
   }
   if (n == 0) return OMERF_OK;
   OMERF_LAUNCH_FAULT();

@@ -99,3 +99,31 @@ def test_host_schedules_match_reference(lib):
         assert lib.omerf_lr_exponential(5e-5, 1e-5, step, 80000) == pytest.approx(adam.lr_exponential(5e-5, 1e-5, step, 80000), rel=1e-6)
     for step in (0, 9999, 10000, 14000, 10 ** 8):
         assert lib.omerf_lambda_occ(step) == pytest.approx(adam.lambda_occ(step), rel=1e-6)
+
+
+def test_camera_validation_without_gpu(lib):
+    """Host cameras with a non-finite pose or intrinsics, or a singular
+    rotation (rays without direction), are rejected with OMERF_EINVAL before
+    any pointer is inspected or anything launched."""
+    import paper_2404_09531_gb300.binding as b
+    d = b._SceneDesc()
+    d.aabb[:] = [-1, 1, -1, 1, -0.1, 0.1]
+    d.grid_res[:] = [4, 4, 4]
+    d.plane_res[:] = [4, 4, 4]
+    d.occ_res = 2
+    d.step = 2.0 ** -8
+    d.eps_occ = 0.01
+    d.n_max = 16
+    d.grid = d.plane_xy = d.plane_xz = d.plane_yz = d.occ = d.mlp = 1 << 20
+    good = {"c2w": [[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 2]], "fx": 8.0, "fy": 8.0, "cx": 4.0, "cy": 4.0,
+            "width": 8, "height": 8}
+    bad = [dict(good, fx=float("inf")), dict(good, cy=float("nan")),
+           dict(good, c2w=[[1, 0, 0, 0], [0, float("nan"), 0, 0], [0, 0, 1, 2]]),
+           dict(good, c2w=[[1, 0, 0, 0], [1, 0, 0, 0], [0, 0, 1, 2]]),   # singular: rows 0 and 1 equal
+           dict(good, c2w=[[0, 0, 0, 0], [0, 0, 0, 0], [0, 0, 0, 2]])]
+    for cam in bad:
+        cs = b.camera_struct(cam)
+        rc = lib.omerf_render_noalloc(ctypes.byref(d), ctypes.byref(cs), None, 64, ctypes.c_void_p(1 << 20), None,
+                                      None)
+        assert rc == -1, cam
+    assert b"camera" in lib.omerf_last_error()

@@ -367,3 +367,25 @@ def test_render_cameras_in_one_launch():
     torch.cuda.synchronize()
     ref17 = torch.cat([parts[1][0]] * 17 + [parts[0][0]])
     assert torch.equal(rgb17, ref17)
+
+
+def test_non_finite_rays_return_background():
+    """Rays with a NaN or infinite component evaluate no sample on either side
+    and return the background (the kernel skips their lattice scan)."""
+    sc = synth.make_scene(1)
+    bg = (0.3, 0.2, 0.1)
+    scene = gpu_scene(sc, bg=bg)
+    good = edge_rays(sc["spec"], n_random=40)[:40]
+    rays = good.copy()
+    nan, inf = np.float32("nan"), np.float32("inf")
+    rays[0, 0] = nan
+    rays[1, 4] = nan
+    rays[2, 2] = inf
+    rays[3, 3:] = [inf, 0.0, 0.0]
+    rays[4, 5] = -inf
+    rgb, cnt = _render_np(scene, rays=rays)
+    ref = oracle.render(oracle.OracleScene(sc, bg=bg), rays)
+    assert np.all(cnt[:5] == 0) and np.all(ref["count"][:5] == 0)
+    np.testing.assert_array_equal(rgb[:5], np.tile(np.float32(bg), (5, 1)))
+    compare_render(rgb[5:], cnt[5:], {k: (v[5:] if hasattr(v, "shape") else v) for k, v in ref.items()},
+                   what="finite rays")
