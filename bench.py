@@ -663,6 +663,23 @@ def run_native(args):
         tr_ms.append(a.elapsed_time(b))
     t_train = float(np.mean(tr_ms))
     loss = res["loss"].cpu().numpy().tolist()
+    # the same step with the deferred-MLP backward on tcgen05 tensor cores
+    # (the alternative the library selects with OMERF_MLP_BWD=tcgen05)
+    os.environ["OMERF_MLP_BWD"] = "tcgen05"
+    tc_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        for g in grads.values():
+            g.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        om.train_step(tscene, rays_d, target, dirs_d, lam=lam, grads=grads, saved=saved)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            tc_ms.append(a.elapsed_time(b))
+    del os.environ["OMERF_MLP_BWD"]
+    t_train_tc = float(np.mean(tc_ms))
     dp_train = None
     if ws > 1:
         # ray-sharded data parallelism (weak scaling): a global batch of ws x
@@ -782,6 +799,11 @@ def run_native(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "train": {"metric": "Mrays/s fwd+bwd train", "value": (1 << 18) / (t_train * 1e-3) / 1e6,
                   "unit": "Mrays/s", "ms_per_step": t_train, "rays_per_step": 1 << 18, "loss": loss,
+                  "mlp_bwd_tcgen05": {"value": (1 << 18) / (t_train_tc * 1e-3) / 1e6, "unit": "Mrays/s",
+                                      "ms_per_step": t_train_tc,
+                                      "note": "the same fused step with the deferred-MLP backward as tcgen05 "
+                                              "products (128-ray tiles, TMEM accumulators): slower than the "
+                                              "default warp-level form, which the line's value uses"},
                   "with_adam": {"value": (1 << 18) / (t_loop * 1e-3) / 1e6, "unit": "Mrays/s",
                                 "ms_per_step": t_loop,
                                 "note": "fwd + bwd + sparsity and entropy terms + fused Adam (lr decay, "

@@ -34,6 +34,7 @@ void set_error(const char* fmt, ...);
 // runtime.cu: device error word, fault injection, profiler ranges.
 constexpr unsigned kErrExtractWait = 1u;   // brick extraction: a tensor load did not complete in time
 constexpr unsigned kErrExtractDrain = 2u;  // ... nor the copy in flight when the CTA gave up
+constexpr unsigned kErrMlpWait = 4u;       // MLP backward: a tensor-core product did not complete in time
 // Device alias of the process-wide error word (page-locked, mapped host
 // memory; allocated by the first call), or NULL if it could not be allocated.
 unsigned* device_error_word();

@@ -16,9 +16,13 @@
 //     (A_<=i = prefix sum of w x, by a lane scan), then chains through Eq. 3
 //     and Eq. 6 and scatter-adds into the grid, planes and z-bounds with
 //     vector float atomics.  No per-sample state is stored between passes.
+#include <cstdlib>
+#include <cstring>
+
 #include "internal.h"
 #include "mma_tf32.cuh"
 #include "packed.cuh"
+#include "tc.cuh"
 
 namespace omerf {
 
@@ -45,6 +49,8 @@ struct BwdArgs {
   float* g_mlp;
   float* loss;  // device [4] or NULL: the Charbonnier and smoothness terms are added (fused step)
   unsigned* counter;
+  unsigned* err;  // device error word of bounded waits (NULL: not reported)
+  int wait_tries; // polls of a bounded mbarrier wait (tcgen05 MLP backward)
 };
 
 // ---------------------------------------------------------------------------
@@ -746,6 +752,428 @@ __global__ void __launch_bounds__(kBwdThreads, 4) mlp_bwd_kernel(const Geo g, co
   }
 }
 
+// ---------------------------------------------------------------------------
+// Kernel 1, fifth-generation tensor-core form (tcgen05).  One CTA of 128
+// threads per tile of 128 consecutive rays: thread t owns ray t of the tile
+// and row t of every product (TMEM lane t).  Each layer of the MLP and of
+// its backward is one M = 128 product, D = A B, with A the tile's staged
+// rows in shared memory and B a weight matrix; one thread issues it as
+// kind::tf32 products with split operands (A_lo B_hi + A_hi B_lo + A_hi B_hi,
+// about FP32 accurate, as in the mma.sync form), commits it to an mbarrier,
+// and every thread reads its row of the FP32 accumulator from TMEM.  The
+// weight gradient sum_rays act (x) delta is one more product per evaluation
+// whose reduction dimension is the tile's 128 rays: A = the staged
+// activation rows read MN-major, B = the staged delta rows read MN-major,
+// accumulating in TMEM for the CTA's whole run, read once at the end.  The
+// tensor core takes MN-major operands in 16-bit formats only, so this
+// product runs as kind::f16 on BF16 copies split the same way (hi + lo,
+// 16 significant bits, three products: relative error ~2^-16, far inside the
+// 1e-3 bar of the gradients; the TF32 layers keep the loss FP32 accurate).
+//
+// Staged rows (the tc.cuh layouts):
+//   act   [128][76] TF32 hi / lo: x 0..33 (34..39 zero), h1 40..55, h2 56..71, 1 at 72 (live rays), 73..75 zero
+//   delta [128][40] TF32 hi / lo: g1 0..15, g2 16..31, g3 32..34, 35..39 zero
+//   actb  [128][80], deltab [128][48]: BF16 hi / lo copies of the same columns (actb 73..79, deltab 35..47 zero)
+// Weight operands (K-major B, [N rows][K], TF32 hi / lo):
+//   W1B [16 units][40 inputs] = W1        W2B [16][16] = W2     W3B [16 (3 used)][16] = W3
+//   W3T [16 u2][8 (3 used)]   = W3^T      W2T [16][16] = W2^T   W1T [16 (7 used)][16 u] = W1[:, :7]^T
+// The M = 128 weight-gradient product reads 128 activation columns per ray;
+// the columns beyond 80 are the next rays' data and land in accumulator
+// rows that are never read.
+namespace tcmlp {
+constexpr int kRows = 128;
+constexpr int kActW = 76, kH1 = 40, kH2 = 56, kOne = 72;
+constexpr int kDelW = 40, kG1 = 0, kG2 = 16, kG3 = 32;
+constexpr int kActBytes = kRows * kActW * 4, kDelBytes = kRows * kDelW * 4;
+constexpr int kW1B = 0, kW2B = kW1B + 16 * 40 * 4, kW3B = kW2B + 16 * 16 * 4, kW3T = kW3B + 16 * 16 * 4,
+              kW2T = kW3T + 16 * 8 * 4, kW1T = kW2T + 16 * 16 * 4, kWBytes = kW1T + 16 * 16 * 4;
+constexpr int kActBW = 80, kDelBW = 48;
+constexpr int kActBBytes = kRows * kActBW * 2, kDelBBytes = kRows * kDelBW * 2;
+constexpr int kActHi = 0, kActLo = kActBytes, kDelHi = 2 * kActBytes, kDelLo = kDelHi + kDelBytes,
+              kActBHi = kDelLo + kDelBytes, kActBLo = kActBHi + kActBBytes, kDelBHi = kActBLo + kActBBytes,
+              kDelBLo = kDelBHi + kDelBBytes, kWHi = kDelBLo + kDelBBytes, kWLo = kWHi + kWBytes,
+              kSmem = kWLo + kWBytes;
+constexpr uint32_t kTmemCols = 128, kColL = 0, kColW = 64;
+constexpr int kTries = 1 << 24;  // bounded mbarrier wait (a product takes well under a microsecond)
+
+// Write v (TF32 hi and lo) at (row, col) of a staged tile of width W.
+__device__ __forceinline__ void put(unsigned char* hi, unsigned char* lo, int row, int col, int W, float v) {
+  uint32_t h, l;
+  split_tf32(v, h, l);
+  const uint32_t o = tc::off4(row, col, W);
+  *reinterpret_cast<uint32_t*>(hi + o) = h;
+  *reinterpret_cast<uint32_t*>(lo + o) = l;
+}
+
+// Four consecutive columns (col % 4 == 0) with one 16-byte store per copy.
+__device__ __forceinline__ void put4(unsigned char* hi, unsigned char* lo, int row, int col, int W, float v0,
+                                     float v1, float v2, float v3) {
+  uint32_t h[4], l[4];
+  split_tf32(v0, h[0], l[0]);
+  split_tf32(v1, h[1], l[1]);
+  split_tf32(v2, h[2], l[2]);
+  split_tf32(v3, h[3], l[3]);
+  const uint32_t o = tc::off4(row, col, W);
+  *reinterpret_cast<uint4*>(hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Eight consecutive columns (col % 8 == 0) of a BF16 tile, hi and lo copies.
+__device__ __forceinline__ void putb8(unsigned char* hi, unsigned char* lo, int row, int col, int W, const float v[8]) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * i]), h1 = __float2bfloat16_rn(v[2 * i + 1]);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
+    h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+  }
+  const uint32_t o = tc::off2(row, col, W);
+  *reinterpret_cast<uint4*>(hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+}  // namespace tcmlp
+
+__global__ void __launch_bounds__(128, 1) mlp_bwd_tc_kernel(const Geo g, const BwdArgs a) {
+  using namespace tcmlp;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float sL[2][4];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char *act_hi = sm + kActHi, *act_lo = sm + kActLo, *del_hi = sm + kDelHi, *del_lo = sm + kDelLo;
+  unsigned char *actb_hi = sm + kActBHi, *actb_lo = sm + kActBLo, *delb_hi = sm + kDelBHi, *delb_lo = sm + kDelBLo;
+  unsigned char *w_hi = sm + kWHi, *w_lo = sm + kWLo;
+  // the BF16 delta columns 35..47 stay zero (only 0..34 are staged)
+  for (int i = tid; i < 2 * kDelBBytes / 16; i += kRows)
+    reinterpret_cast<uint4*>(delb_hi)[i] = make_uint4(0u, 0u, 0u, 0u);
+  const uint32_t s_base = tc::smem_u32(sm), s_bar = tc::smem_u32(&bar);
+  const float* W = g.mlp;
+  // weight operands (the tile-independent B matrices), TF32 hi / lo
+  for (int i = tid; i < 16 * 40; i += kRows) {
+    const int u = i / 40, c = i % 40;
+    put(w_hi + kW1B, w_lo + kW1B, u, c, 40, c < 34 ? W[kOffW1 + u * 34 + c] : 0.0f);
+  }
+  for (int i = tid; i < 16 * 16; i += kRows) {
+    const int r = i / 16, c = i % 16;
+    put(w_hi + kW2B, w_lo + kW2B, r, c, 16, W[kOffW2 + r * 16 + c]);           // W2[u2][u1]
+    put(w_hi + kW3B, w_lo + kW3B, r, c, 16, r < 3 ? W[kOffW3 + r * 16 + c] : 0.0f);  // W3[o][u2]
+    put(w_hi + kW2T, w_lo + kW2T, r, c, 16, W[kOffW2 + c * 16 + r]);           // [u1][u2] = W2[u2][u1]
+    put(w_hi + kW1T, w_lo + kW1T, r, c, 16, r < 7 ? W[kOffW1 + c * 34 + r] : 0.0f);  // [i][u] = W1[u][i]
+  }
+  for (int i = tid; i < 16 * 8; i += kRows) {
+    const int r = i / 8, c = i % 8;
+    put(w_hi + kW3T, w_lo + kW3T, r, c, 8, c < 3 ? W[kOffW3 + c * 16 + r] : 0.0f);  // [u2][o] = W3[o][u2]
+  }
+  float b1[16], b2[16], b3[3];
+#pragma unroll
+  for (int j = 0; j < 16; j++) {
+    b1[j] = __ldg(W + kOffB1 + j);
+    b2[j] = __ldg(W + kOffB2 + j);
+  }
+#pragma unroll
+  for (int j = 0; j < 3; j++) b3[j] = __ldg(W + kOffB3 + j);
+  if (warp == 0) tc::alloc(&tmem_base, kTmemCols);
+  if (tid == 0) tc::mbar_init(s_bar, 1);
+  tc::fence_proxy();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t my_lane = tmem + ((uint32_t)(32 * warp) << 16);
+  const float gs = a.grad_scale ? __ldg(a.grad_scale) : 1.0f;
+  const bool want_dw = a.g_mlp != nullptr;
+  const long n_tiles = (a.n + kRows - 1) / kRows;
+  uint32_t phase = 0;
+  bool dw_started = false, failed = false;
+  float l_rgb = 0.0f, l_smooth = 0.0f;
+
+  // Sync the staged rows, let thread 0 issue the products, wait for them.
+  // Returns false (on every thread) if the wait ran out: the error word is
+  // set and the products still in flight are waited for (bounded).
+  auto round_trip = [&](auto issue) -> bool {
+    tc::fence_proxy();
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      issue();
+      tc::commit(s_bar);
+    }
+    bool ok = tc::mbar_wait(s_bar, phase, a.wait_tries);
+    if (__syncthreads_or(!ok)) {
+      if (!ok) tc::mbar_wait(s_bar, phase, kTries);
+      if (tid == 0 && a.err) {
+        atomicOr_system(a.err, kErrMlpWait);
+        __threadfence_system();
+      }
+      failed = true;
+      return false;
+    }
+    phase ^= 1u;
+    tc::fence_after();
+    return true;
+  };
+  const uint32_t id16 = tc::idesc(2, 128, 16);
+  const uint32_t idw = tc::idesc(1, 128, 48, 1, 1);  // BF16, both operands MN-major
+  const int sAct = (kActW / 4) * 128, sDel = (kDelW / 4) * 128;
+  // three TF32 products per K-step of K-major operands into accumulator column col
+  auto mma3k = [&](uint32_t col, int a_off, int a_sbo, int a_lo_shift, int b_off, int b_sbo, int ksteps,
+                   uint32_t id) {
+    for (int k = 0; k < ksteps; k++) {
+      const uint64_t ah = tc::desc(s_base + a_off + 256 * k, 128, a_sbo);
+      const uint64_t al = tc::desc(s_base + a_off + a_lo_shift + 256 * k, 128, a_sbo);
+      const uint64_t bh = tc::desc(s_base + kWHi + b_off + 256 * k, 128, b_sbo);
+      const uint64_t bl = tc::desc(s_base + kWLo + b_off + 256 * k, 128, b_sbo);
+      tc::mma_tf32(tmem + col, al, bh, id, k > 0);
+      tc::mma_tf32(tmem + col, ah, bl, id, true);
+      tc::mma_tf32(tmem + col, ah, bh, id, true);
+    }
+  };
+  // the weight-gradient product of the staged tile, accumulated in TMEM
+  auto mma_dw = [&]() {
+    constexpr int lA = (kActBW / 8) * 128, lD = (kDelBW / 8) * 128;  // next 8 rays (K)
+    for (int k = 0; k < kRows / 16; k++) {  // 16 rays per product
+      const uint64_t ah = tc::desc(s_base + kActBHi + 2 * k * lA, lA, 128);
+      const uint64_t al = tc::desc(s_base + kActBLo + 2 * k * lA, lA, 128);
+      const uint64_t dh = tc::desc(s_base + kDelBHi + 2 * k * lD, lD, 128);
+      const uint64_t dl = tc::desc(s_base + kDelBLo + 2 * k * lD, lD, 128);
+      tc::mma_f16(tmem + kColW, al, dh, idw, dw_started || k > 0);
+      tc::mma_f16(tmem + kColW, ah, dl, idw, true);
+      tc::mma_f16(tmem + kColW, ah, dh, idw, true);
+    }
+  };
+  // staged x row (and the ones column) of this thread's ray
+  auto stage_x = [&](bool live, const float F[7], const float dir[3]) {
+    float x[40];
+#pragma unroll
+    for (int i = 0; i < 40; i++) x[i] = 0.0f;
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < 7; i++) x[i] = F[i];
+      view_encoding(dir, x + 7);
+    }
+#pragma unroll
+    for (int c = 0; c < 40; c += 4) put4(act_hi, act_lo, tid, c, kActW, x[c], x[c + 1], x[c + 2], x[c + 3]);
+#pragma unroll
+    for (int c = 0; c < 40; c += 8) putb8(actb_hi, actb_lo, tid, c, kActBW, x + c);
+    const float one[8] = {live ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    put4(act_hi, act_lo, tid, kOne, kActW, one[0], 0.0f, 0.0f, 0.0f);
+    putb8(actb_hi, actb_lo, tid, kOne, kActBW, one);
+  };
+  // 16 values at column col of the activation (act = true) or delta rows, TF32 and BF16
+  auto stage16 = [&](bool act, int col, const float v[16]) {
+#pragma unroll
+    for (int c = 0; c < 16; c += 4)
+      put4(act ? act_hi : del_hi, act ? act_lo : del_lo, tid, col + c, act ? kActW : kDelW, v[c], v[c + 1], v[c + 2],
+           v[c + 3]);
+    putb8(act ? actb_hi : delb_hi, act ? actb_lo : delb_lo, tid, col, act ? kActBW : kDelBW, v);
+    putb8(act ? actb_hi : delb_hi, act ? actb_lo : delb_lo, tid, col + 8, act ? kActBW : kDelBW, v + 8);
+  };
+  // forward of the staged x: h1, h2 staged and returned, y = G
+  auto forward = [&](float h1[16], float h2[16], float y[3]) -> bool {
+    float t[16];
+    if (!round_trip([&] { mma3k(kColL, kActHi, sAct, kActLo - kActHi, kW1B, 1280, 5, id16); })) return false;
+    tc::ld16(my_lane + kColL, t);
+#pragma unroll
+    for (int j = 0; j < 16; j++) h1[j] = fmaxf(t[j] + b1[j], 0.0f);
+    stage16(true, kH1, h1);
+    if (!round_trip([&] { mma3k(kColL, kActHi + (kH1 / 4) * 128, sAct, kActLo - kActHi, kW2B, 512, 2, id16); }))
+      return false;
+    tc::ld16(my_lane + kColL, t);
+#pragma unroll
+    for (int j = 0; j < 16; j++) h2[j] = fmaxf(t[j] + b2[j], 0.0f);
+    stage16(true, kH2, h2);
+    if (!round_trip([&] { mma3k(kColL, kActHi + (kH2 / 4) * 128, sAct, kActLo - kActHi, kW3B, 512, 2, id16); }))
+      return false;
+    tc::ld16(my_lane + kColL, t);
+#pragma unroll
+    for (int j = 0; j < 3; j++) y[j] = sigmoidf_(t[j] + b3[j]);
+    return true;
+  };
+  // backward of the evaluation whose activations are staged (h1, h2 its ReLU
+  // outputs): deltas staged, the weight gradient accumulated, dL/dF added to gF
+  auto backward = [&](const float h1[16], const float h2[16], const float y[3], const float gy[3],
+                      float gF[7]) -> bool {
+    float t[16];
+    const float g3[8] = {gy[0] * y[0] * (1.0f - y[0]), gy[1] * y[1] * (1.0f - y[1]), gy[2] * y[2] * (1.0f - y[2]),
+                         0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    put4(del_hi, del_lo, tid, kG3, kDelW, g3[0], g3[1], g3[2], 0.0f);
+    put4(del_hi, del_lo, tid, kG3 + 4, kDelW, 0.0f, 0.0f, 0.0f, 0.0f);
+    putb8(delb_hi, delb_lo, tid, kG3, kDelBW, g3);
+    if (!round_trip([&] { mma3k(kColL, kDelHi + (kG3 / 4) * 128, sDel, kDelLo - kDelHi, kW3T, 256, 1, id16); }))
+      return false;
+    tc::ld16(my_lane + kColL, t);
+#pragma unroll
+    for (int j = 0; j < 16; j++) t[j] = h2[j] > 0.0f ? t[j] : 0.0f;
+    stage16(false, kG2, t);
+    if (!round_trip([&] { mma3k(kColL, kDelHi + (kG2 / 4) * 128, sDel, kDelLo - kDelHi, kW2T, 512, 2, id16); }))
+      return false;
+    tc::ld16(my_lane + kColL, t);
+#pragma unroll
+    for (int j = 0; j < 16; j++) t[j] = h1[j] > 0.0f ? t[j] : 0.0f;
+    stage16(false, kG1, t);
+    if (!round_trip([&] {
+          mma3k(kColL, kDelHi + (kG1 / 4) * 128, sDel, kDelLo - kDelHi, kW1T, 512, 2, id16);
+          if (want_dw) mma_dw();
+        }))
+      return false;
+    dw_started = dw_started || want_dw;
+    tc::ld16(my_lane + kColL, t);
+#pragma unroll
+    for (int i = 0; i < 7; i++) gF[i] += t[i];
+    return true;
+  };
+
+  for (long tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+    const long rid = tile * kRows + tid;
+    const bool valid = rid < a.n;
+    float d[3] = {0.0f, 0.0f, 1.0f}, F[7] = {0, 0, 0, 0, 0, 0, 0}, TN = 1.0f;
+    int cnt = 0;
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) d[c] = __ldg(a.rays + 6 * rid + 3 + c);
+      const float4* sv = reinterpret_cast<const float4*>(a.saved + (long)kSavedFloats * rid);
+      const float4 s0 = __ldg(sv), s1 = __ldg(sv + 1), s2 = __ldg(sv + 2);
+      F[0] = s0.x; F[1] = s0.y; F[2] = s0.z; F[3] = s0.w;
+      F[4] = s1.x; F[5] = s1.y; F[6] = s1.z; TN = s1.w;
+      cnt = __float_as_int(s2.x);
+    }
+    const bool live = valid && cnt > 0;
+    float gF[7] = {0, 0, 0, 0, 0, 0, 0};
+    float gC[3] = {0, 0, 0}, yd[3], gyd[3] = {0, 0, 0}, h1d[16], h2d[16];
+    stage_x(live, F, d);
+    if (!forward(h1d, h2d, yd)) break;
+    if (live) {
+      float e[3], e2 = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        e[j] = F[j] + yd[j] + TN * g.bg[j] - __ldg(a.target + 3 * rid + j);
+        e2 = fmaf(e[j], e[j], e2);
+      }
+      const float ell = sqrtf(e2 + 1e-6f);
+      const float inv_ell = 1.0f / ell;
+      l_rgb += ell;
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        gC[j] = gs * a.lam_rgb * e[j] * inv_ell;
+        gyd[j] = gC[j];
+      }
+    } else if (valid && a.loss) {
+      float e2 = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        const float e = g.bg[j] - __ldg(a.target + 3 * rid + j);
+        e2 = fmaf(e, e, e2);
+      }
+      l_rgb += sqrtf(e2 + 1e-6f);
+    }
+    // smoothness evaluations (Eqs. 9-10), each backpropagated at once
+    const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    bool ok = true;
+    for (int k = 0; k < a.K && ok; k++) {
+      float sh[3] = {0.0f, 0.0f, 1.0f}, S_cos = 0.0f;
+      if (live) {
+        const float* sp = a.dirs + 3 * ((long)rid * a.K + k);
+        const float sv[3] = {__ldg(sp), __ldg(sp + 1), __ldg(sp + 2)};
+        const float sn = sqrtf(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
+        S_cos = (d[0] * sv[0] + d[1] * sv[1] + d[2] * sv[2]) / (dn * sn);
+#pragma unroll
+        for (int c = 0; c < 3; c++) sh[c] = sv[c] / sn;
+      }
+      float h1[16], h2[16], ys[3], gys[3] = {0.0f, 0.0f, 0.0f};
+      stage_x(live, F, sh);
+      ok = forward(h1, h2, ys);
+      if (!ok) break;
+      if (live) {
+        float q = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          gys[j] = gs * a.lam_smooth * 2.0f * S_cos * (ys[j] - yd[j]);
+          gyd[j] -= gys[j];
+          q = fmaf(ys[j] - yd[j], ys[j] - yd[j], q);
+        }
+        l_smooth = fmaf(S_cos, q, l_smooth);
+      }
+      ok = backward(h1, h2, ys, gys, gF);
+    }
+    if (!ok) break;
+    // the evaluation at d: its activations re-staged from registers
+    if (a.K > 0) {
+      stage_x(live, F, d);
+      stage16(true, kH1, h1d);
+      stage16(true, kH2, h2d);
+    }
+    if (!backward(h1d, h2d, yd, gyd, gF)) break;
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < 3; j++) gF[j] += gC[j];
+      const float gT = gC[0] * g.bg[0] + gC[1] * g.bg[1] + gC[2] * g.bg[2];
+      float4* sv = reinterpret_cast<float4*>(a.saved + (long)kSavedFloats * rid);
+      sv[3] = make_float4(gF[0], gF[1], gF[2], gF[3]);
+      sv[4] = make_float4(gF[4], gF[5], gF[6], gT);
+    }
+  }
+  // loss terms of a fused step: warp sums -> CTA sum -> one global add per CTA
+  if (a.loss) {
+    l_rgb = warp_sum(l_rgb);
+    l_smooth = warp_sum(l_smooth);
+    if (lane == 0) {
+      sL[0][warp] = l_rgb;
+      sL[1][warp] = l_smooth;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float s0 = 0.0f, s1 = 0.0f;
+      for (int w = 0; w < kRows / 32; w++) {
+        s0 += sL[0][w];
+        s1 += sL[1][w];
+      }
+      s0 *= a.lam_rgb;
+      s1 *= a.lam_smooth;
+      atomicAdd(a.loss + 1, s0);
+      atomicAdd(a.loss + 2, s1);
+      atomicAdd(a.loss + 0, s0 + s1);
+    }
+  }
+  // weight gradient: accumulator row m = activation column m, column n =
+  // delta column n; each thread reads its row and adds the entries that are
+  // parameters of Eq. 4's MLP
+  if (dw_started && !failed) {
+    float v[48];
+    tc::ld16(my_lane + kColW, v);
+    tc::ld16(my_lane + kColW + 16, v + 16);
+    tc::ld16(my_lane + kColW + 32, v + 32);
+    const int m = tid;
+    float* G = a.g_mlp;
+    if (m < 34) {
+#pragma unroll
+      for (int u = 0; u < 16; u++) atomicAdd(G + kOffW1 + u * 34 + m, v[kG1 + u]);
+    } else if (m >= kH1 && m < kH1 + 16) {
+#pragma unroll
+      for (int u2 = 0; u2 < 16; u2++) atomicAdd(G + kOffW2 + u2 * 16 + (m - kH1), v[kG2 + u2]);
+    } else if (m >= kH2 && m < kH2 + 16) {
+#pragma unroll
+      for (int o = 0; o < 3; o++) atomicAdd(G + kOffW3 + o * 16 + (m - kH2), v[kG3 + o]);
+    } else if (m == kOne) {
+#pragma unroll
+      for (int u = 0; u < 16; u++) {
+        atomicAdd(G + kOffB1 + u, v[kG1 + u]);
+        atomicAdd(G + kOffB2 + u, v[kG2 + u]);
+      }
+#pragma unroll
+      for (int o = 0; o < 3; o++) atomicAdd(G + kOffB3 + o, v[kG3 + o]);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::dealloc(tmem, kTmemCols);
+  }
+}
+
 // Kernel 2: re-march every ray (one warp per bundle of 32 rays, persistent)
 // and scatter the per-sample gradients.
 #ifndef OMERF_BWD_MINB
@@ -811,7 +1239,31 @@ static cudaError_t launch_bwd_variant(const omerf_scene* s, const BwdArgs& a, cu
   return cudaGetLastError();
 }
 
+static cudaError_t launch_mlp_bwd_tc(const omerf_scene* s, const BwdArgs& a, cudaStream_t stream) {
+  static std::atomic<int> ready[64];  // per device: shared-memory attribute set
+  const int dev = s->device & 63;
+  if (!ready[dev].load(std::memory_order_relaxed)) {
+    cudaFuncSetAttribute((const void*)mlp_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcmlp::kSmem);
+    ready[dev].store(1, std::memory_order_relaxed);
+  }
+  const long tiles = (a.n + tcmlp::kRows - 1) / tcmlp::kRows;
+  const int grid = (int)(tiles < s->num_sms ? tiles : s->num_sms);
+  mlp_bwd_tc_kernel<<<grid < 1 ? 1 : grid, tcmlp::kRows, tcmlp::kSmem, stream>>>(s->geo, a);
+  return cudaGetLastError();
+}
+
+// The deferred-MLP backward runs as warp-level mma.sync products (16 warps
+// per SM keep the small per-ray products busy); OMERF_MLP_BWD=tcgen05 in the
+// environment selects the tcgen05 form instead (one 128-ray tile per SM in
+// flight: about three times slower on these 16-unit layers, kept as a
+// tested alternative).
+static bool mlp_bwd_tcgen05() {
+  const char* v = std::getenv("OMERF_MLP_BWD");
+  return v && std::strcmp(v, "tcgen05") == 0;
+}
+
 static cudaError_t launch_mlp_bwd(const omerf_scene* s, const BwdArgs& a, cudaStream_t stream) {
+  if (mlp_bwd_tcgen05()) return launch_mlp_bwd_tc(s, a, stream);
   const size_t smem = sizeof(MlpBwdShared) + (size_t)(kBwdThreads / 32) * 32 * kRow * sizeof(float);
   static std::atomic<int> blocks[64];  // per device: resident CTAs
   const int dev = s->device & 63;
@@ -850,6 +1302,10 @@ cudaError_t launch_march_bwd(const omerf_scene* s, const float* rays, const floa
   a.g_yz = g_yz;
   a.g_occ = g_occ;
   a.g_mlp = g_mlp;
+  a.err = device_error_word();
+  // OMERF_FAULT=mlp_wait: the tcgen05 MLP backward's first wait gives up at
+  // once (its products still complete and are waited for), for tests
+  a.wait_tries = fault_injected("mlp_wait") ? 0 : tcmlp::kTries;
   if (a.n_bundles == 0) return cudaSuccess;
   cudaError_t e = launch_mlp_bwd(s, a, stream);
   if (e != cudaSuccess) return e;

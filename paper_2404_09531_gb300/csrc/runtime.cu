@@ -65,9 +65,10 @@ omerf_status take_device_error() {
   if (!h) return OMERF_OK;
   const unsigned v = __atomic_exchange_n(h, 0u, __ATOMIC_SEQ_CST);
   if (!v) return OMERF_OK;
-  set_error("a bounded device-side wait gave up:%s%s; the output of that call is incomplete",
+  set_error("a bounded device-side wait gave up:%s%s%s; the output of that call is incomplete",
             (v & kErrExtractWait) ? " brick extraction waited too long for a tensor copy" : "",
-            (v & kErrExtractDrain) ? " (and for the copy still in flight)" : "");
+            (v & kErrExtractDrain) ? " (and for the copy still in flight)" : "",
+            (v & kErrMlpWait) ? " the MLP backward waited too long for a tensor-core product" : "");
   return OMERF_ETIMEOUT;
 }
 
