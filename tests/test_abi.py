@@ -127,3 +127,25 @@ def test_camera_validation_without_gpu(lib):
                                       None)
         assert rc == -1, cam
     assert b"camera" in lib.omerf_last_error()
+
+
+def test_new_entry_points_validate_on_the_host(lib):
+    """Arguments the new entry points reject before touching the GPU."""
+    FAKE = ctypes.c_void_p(1 << 20)
+    f6 = (ctypes.c_float * 6)(-1, 1, -1, 1, -0.1, 0.1)
+    g3 = (ctypes.c_int32 * 3)(16, 16, 8)
+    # grow: NULL old table / missing counter, table aliasing old_table, bad brick edge
+    assert lib.omerf_grow_brick_table(f6, g3, 4, FAKE, 4, None, FAKE, FAKE, FAKE, None) == -1
+    assert lib.omerf_grow_brick_table(f6, g3, 4, FAKE, 4, FAKE, FAKE, FAKE, None, None) == -1
+    assert lib.omerf_grow_brick_table(f6, g3, 4, FAKE, 4, FAKE, FAKE, FAKE, FAKE, None) == -1  # table == old_table
+    assert lib.omerf_grow_brick_table(f6, g3, 3, FAKE, 4, ctypes.c_void_p(2 << 20), FAKE, FAKE, FAKE, None) == -1
+    # load probe: slice sizes must be whole 256-thread x 32-byte sweeps, buffers aligned
+    assert lib.omerf_probe_load_bandwidth(FAKE, 4096, 4, 1, FAKE, None) == -2
+    assert lib.omerf_probe_load_bandwidth(FAKE, 8192 + 16, 4, 1, FAKE, None) == -2
+    assert lib.omerf_probe_load_bandwidth(FAKE, 8192, 0, 1, FAKE, None) == -2
+    assert lib.omerf_probe_load_bandwidth(ctypes.c_void_p((1 << 20) + 16), 8192, 4, 1, FAKE, None) == -1
+    assert lib.omerf_probe_load_bandwidth(None, 8192, 4, 1, FAKE, None) == -1
+    # checking-build counters: a NULL scene or output
+    counts = (ctypes.c_uint64 * 2)()
+    assert lib.omerf_check_counts(None, counts, 0, None) == -1
+    assert lib.omerf_check_build() in (0, 1)
