@@ -438,6 +438,11 @@ int32_t omerf_check_build(void);
  * OMERF_ECHECK if counts[1] > 0, OMERF_EINVAL in the default build (counts 0). */
 omerf_status omerf_check_counts(const omerf_scene *scene, uint64_t counts[2], int32_t reset, void *stream);
 
+/* The counters of every scene destroyed so far in this process, summed
+ * (read back when each is destroyed; counts reset by omerf_check_counts are
+ * not included); zeros in the default build.  Host-only. */
+void omerf_check_totals(uint64_t totals[2]);
+
 /* Thread-local description of the last failure in this thread. */
 const char *omerf_last_error(void);
 

@@ -14,6 +14,7 @@ from .binding import (  # noqa: F401
     build_brick_table,
     camera_struct,
     check_counts,
+    check_totals,
     crop_planes,
     entropy_loss,
     extract_bricks,
@@ -40,7 +41,7 @@ from .binding import (  # noqa: F401
 )
 
 __all__ = [
-    "OmerfError", "Scene", "TrainStep", "Trainer", "adam_step", "build_brick_table", "camera_struct", "check_counts",
+    "OmerfError", "Scene", "TrainStep", "Trainer", "adam_step", "build_brick_table", "camera_struct", "check_counts", "check_totals",
     "crop_planes", "entropy_loss", "extract_bricks", "grow_brick_table", "lambda_occ", "lib", "lr_exponential", "occupancy_grid",
     "plane_crop_rows", "probe_load_bandwidth", "ray_interval", "render", "render_cameras", "render_noalloc", "saved_bytes_per_ray", "scene_from_synth",
     "sparsity_loss", "sync", "train_bwd", "train_fwd", "train_step", "unpack_occupancy_bits", "zero_grads",

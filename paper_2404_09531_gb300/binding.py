@@ -90,6 +90,7 @@ SIGNATURES = {
     "omerf_probe_load_bandwidth": (ctypes.c_int, [_P, _L, _I, _I, _P, _P]),
     "omerf_check_build": (ctypes.c_int32, []),
     "omerf_check_counts": (ctypes.c_int, [_P, _P, _I, _P]),
+    "omerf_check_totals": (None, [_P]),
     "omerf_sync": (ctypes.c_int, [_P, _I]),
     "omerf_last_error": (ctypes.c_char_p, []),
 }
@@ -659,6 +660,15 @@ def check_counts(scene: Scene, reset=True, stream=None):
     or (status -7) if a read fell outside an array."""
     c = (ctypes.c_uint64 * 2)()
     _check(lib().omerf_check_counts(scene.handle, c, int(bool(reset)), _stream(stream)), "omerf_check_counts")
+    return int(c[0]), int(c[1])
+
+
+def check_totals():
+    """The checking build's counters of every scene destroyed so far in this
+    process: (corner reads of unstored bricks, feature reads outside the
+    arrays); zeros in the default build."""
+    c = (ctypes.c_uint64 * 2)()
+    lib().omerf_check_totals(c)
     return int(c[0]), int(c[1])
 
 

@@ -14,6 +14,8 @@
 namespace omerf {
 
 static thread_local char g_err[512] = "";
+// checking build: counts of the scenes destroyed so far in this process
+static std::atomic<unsigned long long> g_check_total[2];
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -543,6 +545,16 @@ omerf_status omerf_scene_update(omerf_scene* s, void* stream) {
 void omerf_scene_destroy(omerf_scene* s) {
   OMERF_API_RANGE();
   if (!s) return;
+  if (s->check) {
+    // the checking build keeps the counts of destroyed scenes (omerf_check_totals)
+    unsigned long long h[2] = {0, 0};
+    if (cudaMemcpy(h, s->check, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      g_check_total[0].fetch_add(h[0]);
+      g_check_total[1].fetch_add(h[1]);
+    } else {
+      cudaGetLastError();
+    }
+  }
   cudaFree(s->state);
   cudaFree(s->counters);
   cudaFree(s->chull);
@@ -817,6 +829,12 @@ omerf_status omerf_sync(void* stream, int32_t timeout_ms) {
 }
 
 int32_t omerf_check_build(void) { return OMERF_CHECK ? 1 : 0; }
+
+void omerf_check_totals(uint64_t totals[2]) {
+  if (!totals) return;
+  totals[0] = g_check_total[0].load();
+  totals[1] = g_check_total[1].load();
+}
 
 omerf_status omerf_check_counts(const omerf_scene* s, uint64_t counts[2], int32_t reset, void* stream) {
   OMERF_API_RANGE();
