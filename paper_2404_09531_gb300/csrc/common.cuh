@@ -264,6 +264,24 @@ struct Texel<__nv_bfloat16> {
   }
 };
 
+// t += w v over the 8 channels of a texel, two channels per packed FP32 FMA
+// (sm_100+; each half is one fused multiply-add rounded to nearest, exactly
+// as fmaf).  Used where the march is issue-bound (BF16 features); with FP32
+// features the scalar form keeps fewer registers live.
+__device__ __forceinline__ void fma8x2(float2 t[4], float w, const float v[8]) {
+  const float2 ww = make_float2(w, w);
+#pragma unroll
+  for (int j = 0; j < 4; j++) t[j] = __ffma2_rn(make_float2(v[2 * j], v[2 * j + 1]), ww, t[j]);
+}
+template <class FT>
+struct Packed {
+  static constexpr bool value = false;
+};
+template <>
+struct Packed<__nv_bfloat16> {
+  static constexpr bool value = true;
+};
+
 // Checking build: count the corners of a stencil whose brick is not stored
 // (they read as zero); the default build does nothing.
 __device__ __forceinline__ void check_unallocated(const Geo& g, const int off[8]) {
@@ -376,35 +394,73 @@ __device__ __forceinline__ const void* plane_base(const Geo& g, int q) {
   return q == 0 ? g.pxy : (q == 1 ? g.pxz : g.pyz);
 }
 
+// The weighted sum of Eq. 2 over the 8 grid corners and 12 plane texels of
+// a stencil (a corner with offset -1 reads zero).
+template <class FT>
+__device__ __forceinline__ void gather_texels(const Geo& g, const int goff[8], const float gw[8], const int poff[12],
+                                              const float pw[12], float t[8]) {
+  if constexpr (Packed<FT>::value) {
+    float2 t2[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) t2[j] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      float v[8];
+      if (goff[c] >= 0 && check_range(g, 0, goff[c])) {
+        Texel<FT>::load(g.grid, goff[c], v);
+        fma8x2(t2, gw[c], v);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      const void* P = plane_base(g, q);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        float v[8];
+        if (!check_range(g, 1 + q, poff[4 * q + c])) continue;
+        Texel<FT>::load(P, poff[4 * q + c], v);
+        fma8x2(t2, pw[4 * q + c], v);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      t[2 * j] = t2[j].x;
+      t[2 * j + 1] = t2[j].y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; c++) t[c] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      float v[8];
+      if (goff[c] >= 0 && check_range(g, 0, goff[c])) {
+        Texel<FT>::load(g.grid, goff[c], v);
+#pragma unroll
+        for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(gw[c], v[ch], t[ch]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      const void* P = plane_base(g, q);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        float v[8];
+        if (!check_range(g, 1 + q, poff[4 * q + c])) continue;
+        Texel<FT>::load(P, poff[4 * q + c], v);
+#pragma unroll
+        for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(pw[4 * q + c], v[ch], t[ch]);
+      }
+    }
+  }
+}
+
 template <class FT, bool SPARSE>
 __device__ __forceinline__ void gather_features(const Geo& g, const float p[3], float t[8]) {
   int goff[8], poff[12];
   float gw[8], pw[12];
   grid_stencil<SPARSE>(g, p, goff, gw);
   plane_stencil(g, p, poff, pw);
-#pragma unroll
-  for (int c = 0; c < 8; c++) t[c] = 0.0f;
-#pragma unroll
-  for (int c = 0; c < 8; c++) {
-    float v[8];
-    if (goff[c] >= 0 && check_range(g, 0, goff[c])) {
-      Texel<FT>::load(g.grid, goff[c], v);
-#pragma unroll
-      for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(gw[c], v[ch], t[ch]);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 3; q++) {
-    const void* P = plane_base(g, q);
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-      float v[8];
-      if (!check_range(g, 1 + q, poff[4 * q + c])) continue;
-      Texel<FT>::load(P, poff[4 * q + c], v);
-#pragma unroll
-      for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(pw[4 * q + c], v[ch], t[ch]);
-    }
-  }
+  gather_texels<FT>(g, goff, gw, poff, pw, t);
 }
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }

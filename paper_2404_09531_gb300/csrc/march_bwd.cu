@@ -485,27 +485,7 @@ __device__ __forceinline__ void march_bundle_bwd(const Geo& g, const BwdArgs& a,
       grid_stencil<SPARSE>(g, p, goff, gw);
       plane_stencil(g, p, poff, pw);
       float t[8];
-#pragma unroll
-      for (int c = 0; c < 8; c++) t[c] = 0.0f;
-#pragma unroll
-      for (int c = 0; c < 8; c++) {
-        if (goff[c] < 0 || !check_range(g, 0, goff[c])) continue;
-        float v[8];
-        Texel<FT>::load(g.grid, goff[c], v);
-#pragma unroll
-        for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(gw[c], v[ch], t[ch]);
-      }
-#pragma unroll
-      for (int q = 0; q < 3; q++) {
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-          float v[8];
-          if (!check_range(g, 1 + q, poff[4 * q + c])) continue;
-          Texel<FT>::load(plane_base(g, q), poff[4 * q + c], v);
-#pragma unroll
-          for (int ch = 0; ch < 8; ch++) t[ch] = fmaf(pw[4 * q + c], v[ch], t[ch]);
-        }
-      }
+      gather_texels<FT>(g, goff, gw, poff, pw, t);
       activate(g, t, p[2], make_float2(qa.w, qb.x), s);
     }
     bool head;
