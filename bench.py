@@ -479,8 +479,10 @@ def measure_load_peaks(om, torch, dev, stream):
     gather's 256-bit read-only load, measured with omerf_probe_load_bandwidth
     in the march's launch shape (3 CTAs of 256 threads per SM): from L1
     (a 16 KB slice per CTA, re-read 4000 times) and from L2 (a 160 KB slice
-    per CTA: 480 KB per SM, beyond L1; 73 MB in all, inside L2).  Best of 5
-    after 3 warm-up launches, CUDA events on the launching stream."""
+    per CTA: 480 KB per SM, beyond L1; 73 MB in all, inside L2); and the
+    rate of the re-march scatter's vector reductions
+    (omerf_probe_red_bandwidth).  Best of 5 after 3 warm-up launches, CUDA
+    events on the launching stream."""
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     ctas = 3 * sms
     out = {}
@@ -500,6 +502,26 @@ def measure_load_peaks(om, torch, dev, stream):
         out[name] = {"gbs": nbytes / (best * 1e-3) / 1e9, "ms": best, "ctas": ctas, "bytes_per_cta": per_cta,
                      "passes": passes}
         del buf, sink
+    # the re-march's gradient scatter: 16-byte vector FP32 reductions, each
+    # lane on its own 128-byte line, in the re-march's launch shape (2 CTAs
+    # of 256 threads per SM) and with twice the warps; 16 KB per warp (40 or
+    # 80 MB in all, inside L2)
+    for name, per_sm, passes in (("red", 2, 256), ("red_4ctas", 4, 128)):
+        rctas, per_warp = per_sm * sms, 16384
+        buf = torch.zeros(rctas * 8 * per_warp // 4, device=dev)
+        for _ in range(3):
+            om.probe_red_bandwidth(buf, per_warp, rctas, passes)
+        best = float("inf")
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nbytes = om.probe_red_bandwidth(buf, per_warp, rctas, passes)
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        out[name] = {"gbs": nbytes / (best * 1e-3) / 1e9, "ms": best, "ctas": rctas, "bytes_per_warp": per_warp,
+                     "passes": passes, "note": "red.global.add.v4.f32, 16 B per lane, every lane its own line"}
+        del buf
     return out
 
 

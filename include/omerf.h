@@ -414,6 +414,23 @@ float omerf_lambda_occ(int64_t step);
 omerf_status omerf_probe_load_bandwidth(const float *buf, int64_t bytes_per_cta, int32_t ctas, int32_t passes,
                                         float *sink, void *stream);
 
+/* Reduction-throughput probe (no counterpart in the paper: the roofline of
+ * the re-march backward, whose gradient scatter of Eqs. 2 and 6-8 adds each
+ * sample's 32-byte texel gradients with 16-byte vector FP32 reductions, one
+ * lane per sample).  ctas CTAs of 256 threads; every warp reduces into its
+ * own bytes_per_warp-byte region of buf, each lane into its own 128-byte
+ * line (16 B per lane, 512 B per warp instruction), stepping through the
+ * region 4 KB at a time, `passes` times; bytes reduced =
+ * ctas * bytes_per_warp * passes.  The caller sizes the regions so that buf
+ * stays inside L2 (the scatter's gradient lines are mostly L2 hits).
+ *   buf   device float32, ctas * 8 * bytes_per_warp bytes, 16-byte aligned;
+ *         every element of each warp's region that a lane hits grows by
+ *         1.0 per pass (contents are otherwise unspecified)
+ *   bytes_per_warp  a positive multiple of 4096, at most 2^24
+ * One kernel launch. */
+omerf_status omerf_probe_red_bandwidth(float *buf, int64_t bytes_per_warp, int32_t ctas, int32_t passes,
+                                       void *stream);
+
 /* Wait for `stream` with a bounded host-side poll; returns OMERF_ETIMEOUT
  * after timeout_ms milliseconds (< 0 waits without limit), OMERF_ECUDA if
  * the stream reported an error. */

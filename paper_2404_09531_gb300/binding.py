@@ -88,6 +88,7 @@ SIGNATURES = {
     "omerf_lr_exponential": (ctypes.c_float, [ctypes.c_float, ctypes.c_float, _L, _L]),
     "omerf_lambda_occ": (ctypes.c_float, [_L]),
     "omerf_probe_load_bandwidth": (ctypes.c_int, [_P, _L, _I, _I, _P, _P]),
+    "omerf_probe_red_bandwidth": (ctypes.c_int, [_P, _L, _I, _I, _P]),
     "omerf_check_build": (ctypes.c_int32, []),
     "omerf_check_counts": (ctypes.c_int, [_P, _P, _I, _P]),
     "omerf_check_totals": (None, [_P]),
@@ -652,6 +653,18 @@ def probe_load_bandwidth(buf: torch.Tensor, bytes_per_cta: int, ctas: int, passe
     _check(lib().omerf_probe_load_bandwidth(_ptr(buf), int(bytes_per_cta), int(ctas), int(passes), _ptr(sink),
                                             _stream(stream)), "omerf_probe_load_bandwidth")
     return int(ctas) * int(bytes_per_cta) * int(passes)
+
+
+def probe_red_bandwidth(buf: torch.Tensor, bytes_per_warp: int, ctas: int, passes: int, stream=None):
+    """Launch the reduction-throughput probe over ``buf`` (float32, at least
+    ctas * 8 * bytes_per_warp bytes; its contents grow); returns the bytes it
+    reduces."""
+    _require_cuda(buf, "buf")
+    if buf.dtype != torch.float32 or buf.numel() * 4 < int(ctas) * 8 * int(bytes_per_warp):
+        raise OmerfError("buf must be float32 with at least ctas * 8 * bytes_per_warp bytes")
+    _check(lib().omerf_probe_red_bandwidth(_ptr(buf), int(bytes_per_warp), int(ctas), int(passes), _stream(stream)),
+           "omerf_probe_red_bandwidth")
+    return int(ctas) * int(bytes_per_warp) * int(passes)
 
 
 def check_counts(scene: Scene, reset=True, stream=None):

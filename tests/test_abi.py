@@ -145,6 +145,13 @@ def test_new_entry_points_validate_on_the_host(lib):
     assert lib.omerf_probe_load_bandwidth(FAKE, 8192, 0, 1, FAKE, None) == -2
     assert lib.omerf_probe_load_bandwidth(ctypes.c_void_p((1 << 20) + 16), 8192, 4, 1, FAKE, None) == -1
     assert lib.omerf_probe_load_bandwidth(None, 8192, 4, 1, FAKE, None) == -1
+    # reduction probe: regions of whole 4 KB steps, a 16-byte aligned buffer
+    assert lib.omerf_probe_red_bandwidth(FAKE, 2048, 4, 1, None) == -2
+    assert lib.omerf_probe_red_bandwidth(FAKE, 4096 + 16, 4, 1, None) == -2
+    assert lib.omerf_probe_red_bandwidth(FAKE, (1 << 24) + 4096, 4, 1, None) == -2
+    assert lib.omerf_probe_red_bandwidth(FAKE, 4096, 4, 0, None) == -2
+    assert lib.omerf_probe_red_bandwidth(ctypes.c_void_p((1 << 20) + 8), 4096, 4, 1, None) == -1
+    assert lib.omerf_probe_red_bandwidth(None, 4096, 4, 1, None) == -1
     # checking-build counters: a NULL scene or output
     counts = (ctypes.c_uint64 * 2)()
     assert lib.omerf_check_counts(None, counts, 0, None) == -1
