@@ -13,8 +13,13 @@
  * Conventions shared by every entry point
  *   - Pointers named "device" point to CUDA device memory owned by the caller
  *     (for example PyTorch tensors); the library never frees them and never
- *     keeps them beyond the scene handle's lifetime.  "host" pointers are
- *     read before the call returns.
+ *     keeps them beyond the scene handle's lifetime.  Before launching, every
+ *     entry point checks on the host (cudaPointerGetAttributes, which
+ *     allocates nothing) that each non-NULL device pointer it was given is
+ *     device or managed memory, and returns OMERF_EDEVICE naming the argument
+ *     otherwise (render outputs may also be page-locked host memory, see
+ *     omerf_render); their sizes cannot be checked and are the caller's.
+ *     "host" pointers are read before the call returns.
  *   - Layouts are channel-last and x-major:
  *       dense grid   [Lx][Ly][Lz][8]
  *       brick pool   [n_bricks][B][B][B][8] with brick table [nbx][nby][nbz]

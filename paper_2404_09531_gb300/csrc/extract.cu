@@ -288,6 +288,8 @@ omerf_status omerf_occupancy_grid(const float aabb[6], const float* occ, int32_t
   const long long blocks = (words + 255) / 256;
   if (blocks > 0x7fffffffLL) { set_error("occupancy grid too large"); return OMERF_ESHAPE; }
   OMERF_LAUNCH_FAULT();
+  omerf_status st = check_device_ptrs({{occ, "occ"}, {bits, "bits"}, {count, "count"}});
+  if (st != OMERF_OK) return st;
   occupancy_grid_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
       reinterpret_cast<const float2*>(occ), M, N[0], N[1], N[2], aabb[4], hz, bits, count);
   cudaError_t e = cudaGetLastError();
@@ -341,6 +343,8 @@ omerf_status omerf_extract_bricks(const int32_t grid_res[3], int32_t brick, cons
       // (the load still completes and is waited for), for tests of the report
       const int tries = fault_injected("extract_wait") ? 0 : (1 << 20);
       OMERF_LAUNCH_FAULT();
+      const omerf_status st = check_device_ptrs({{table, "table"}, {src, "src"}, {pool, "pool"}});
+      if (st != OMERF_OK) return st;
       extract_bricks_tma_kernel<<<blocks, 32, smem, (cudaStream_t)stream>>>(
           map, nb[0], nb[1], nb[2], brick, table, n_bricks, static_cast<unsigned char*>(pool), (unsigned)brick_bytes,
           tries, device_error_word());
@@ -349,6 +353,8 @@ omerf_status omerf_extract_bricks(const int32_t grid_res[3], int32_t brick, cons
     }
   }
   OMERF_LAUNCH_FAULT();
+  const omerf_status st = check_device_ptrs({{table, "table"}, {src, "src"}, {src_table, "src_table"}, {pool, "pool"}});
+  if (st != OMERF_OK) return st;
   const int blocks = grid_for(entries, 1, 16 * sm_count());
   extract_bricks_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(
       grid_res[0], grid_res[1], grid_res[2], brick, nb[0], nb[1], nb[2], table, n_bricks,
@@ -370,6 +376,8 @@ omerf_status omerf_plane_crop_rows(const float plane_z[2], int32_t Rz, const flo
   }
   if (!aligned(occ, 8) || !aligned(rows, 4) || !aligned(z_range, 4)) { set_error("misaligned argument"); return OMERF_EINVAL; }
   OMERF_LAUNCH_FAULT();
+  omerf_status st = check_device_ptrs({{occ, "occ"}, {rows, "rows"}, {z_range, "z_range"}});
+  if (st != OMERF_OK) return st;
   plane_crop_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float2*>(occ), (long long)M * M,
                                                           plane_z[0], plane_z[1], Rz, rows, z_range);
   cudaError_t e = cudaGetLastError();
@@ -389,6 +397,8 @@ omerf_status omerf_crop_planes(const void* src, int64_t n_outer, int32_t Rz, int
   const int words = feat_dtype == OMERF_F32 ? 2 : 1;
   const long long total = (long long)n_outer * (k1 - k0 + 1) * words;
   OMERF_LAUNCH_FAULT();
+  omerf_status st = check_device_ptrs({{src, "src"}, {dst, "dst"}});
+  if (st != OMERF_OK) return st;
   crop_rows_kernel<<<grid_for(total, 256, 8 * sm_count()), 256, 0, (cudaStream_t)stream>>>(
       static_cast<const uint4*>(src), (long long)n_outer, Rz, k0, k1 - k0 + 1, words, static_cast<uint4*>(dst));
   cudaError_t e = cudaGetLastError();

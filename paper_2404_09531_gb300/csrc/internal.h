@@ -2,6 +2,8 @@
 #pragma once
 
 #include <atomic>
+#include <initializer_list>
+#include <utility>
 
 #include "common.cuh"
 #include "omerf.h"
@@ -90,6 +92,10 @@ omerf_status build_brick_neighbors(omerf_scene* s, cudaStream_t stream);
 omerf_status validate_camera(const omerf_camera* c, int64_t n);
 // OMERF_EDEVICE unless p is NULL, device or managed memory.
 omerf_status check_device_ptr(const void* p, const char* name);
+// The same for every (pointer, name) of a list: the arrays an entry point
+// hands to its kernels are checked on the host before anything is launched,
+// since a host address read or written by a kernel would fault the device.
+omerf_status check_device_ptrs(std::initializer_list<std::pair<const void*, const char*>> ptrs);
 // A render output: device memory, or page-locked host memory whose device
 // alias is returned in *dev; anything else is OMERF_EDEVICE.
 omerf_status output_ptr(void* p, void** dev, const char* name);

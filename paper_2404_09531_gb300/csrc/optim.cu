@@ -90,6 +90,12 @@ omerf_status omerf_adam_step(const omerf_adam_group* groups, int32_t n_groups, f
   const long want = (total + 255) / 256;
   const int grid = (int)(want < 8L * sms ? want : 8L * sms);
   OMERF_LAUNCH_FAULT();
+  for (int q = 0; q < n_groups; q++) {
+    const omerf_adam_group& gr = groups[q];
+    const omerf_status st = check_device_ptrs(
+        {{gr.param, "param"}, {gr.grad, "grad"}, {gr.m, "m"}, {gr.v, "v"}, {gr.shadow_bf16, "shadow_bf16"}});
+    if (st != OMERF_OK) return st;
+  }
   adam_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "adam kernel");

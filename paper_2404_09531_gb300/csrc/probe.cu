@@ -64,6 +64,8 @@ extern "C" omerf_status omerf_probe_load_bandwidth(const float* buf, int64_t byt
   }
   if (!aligned(buf, 32) || !aligned(sink, 4)) { set_error("buf must be 32-byte aligned"); return OMERF_EINVAL; }
   OMERF_LAUNCH_FAULT();
+  const omerf_status st = check_device_ptrs({{buf, "buf"}, {sink, "sink"}});
+  if (st != OMERF_OK) return st;
   load_probe_kernel<<<ctas, 256, 0, (cudaStream_t)stream>>>(buf, bytes_per_cta / 4, passes, sink);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "load probe launch");
@@ -80,6 +82,8 @@ extern "C" omerf_status omerf_probe_red_bandwidth(float* buf, int64_t bytes_per_
   }
   if (!aligned(buf, 16)) { set_error("buf must be 16-byte aligned"); return OMERF_EINVAL; }
   OMERF_LAUNCH_FAULT();
+  const omerf_status st = check_device_ptr(buf, "buf");
+  if (st != OMERF_OK) return st;
   red_probe_kernel<<<ctas, 256, 0, (cudaStream_t)stream>>>(buf, bytes_per_warp / 4, passes);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "reduction probe launch");

@@ -229,6 +229,15 @@ omerf_status check_reg_args(const omerf_scene* s, const void* in, int64_t n, flo
   return OMERF_OK;
 }
 
+// The arrays of a regulariser call, checked to be device memory.
+omerf_status check_reg_ptrs(const void* in, const float* grad_scale, const float* loss, const float* const* gp,
+                            int ngp, const float* g_occ) {
+  omerf_status st =
+      check_device_ptrs({{in, "points / rays"}, {grad_scale, "grad_scale"}, {loss, "loss"}, {g_occ, "g_occ"}});
+  for (int i = 0; i < ngp && st == OMERF_OK; i++) st = check_device_ptr(gp[i], "gradient buffer");
+  return st;
+}
+
 template <class K>
 int reg_grid(K kern, long units_per_block, long n, int num_sms) {
   static std::atomic<int> per_sm[64];  // per device: resident CTAs of this kernel
@@ -262,6 +271,7 @@ omerf_status omerf_sparsity_loss(const omerf_scene* s, const float* points, int6
   auto k = bf16 ? (sparse ? sparsity_kernel<__nv_bfloat16, true> : sparsity_kernel<__nv_bfloat16, false>)
                 : (sparse ? sparsity_kernel<float, true> : sparsity_kernel<float, false>);
   OMERF_LAUNCH_FAULT();
+  if ((st = check_reg_ptrs(points, grad_scale, loss, gp, 4, nullptr)) != OMERF_OK) return st;
   k<<<reg_grid(k, kThreads, n, s->num_sms), kThreads, 0, cs>>>(s->geo, points, n, lam_n, grad_scale, loss, G);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "sparsity loss launch");
@@ -283,6 +293,7 @@ omerf_status omerf_entropy_loss(const omerf_scene* s, const float* rays, int64_t
   auto k = bf16 ? (sparse ? entropy_kernel<__nv_bfloat16, true> : entropy_kernel<__nv_bfloat16, false>)
                 : (sparse ? entropy_kernel<float, true> : entropy_kernel<float, false>);
   OMERF_LAUNCH_FAULT();
+  if ((st = check_reg_ptrs(rays, grad_scale, loss, gp, 4, g_occ)) != OMERF_OK) return st;
   k<<<reg_grid(k, rays_per_block, n, s->num_sms), kThreads, 0, cs>>>(s->geo, rays, n, lam_n, grad_scale, loss, G);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "entropy loss launch");

@@ -303,6 +303,14 @@ omerf_status validate_desc(const omerf_scene_desc* d) {
   return OMERF_OK;
 }
 
+omerf_status check_device_ptrs(std::initializer_list<std::pair<const void*, const char*>> ptrs) {
+  for (const auto& pn : ptrs) {
+    const omerf_status st = check_device_ptr(pn.first, pn.second);
+    if (st != OMERF_OK) return st;
+  }
+  return OMERF_OK;
+}
+
 omerf_status check_device_ptr(const void* p, const char* name) {
   if (!p) return OMERF_OK;
   cudaPointerAttributes at;
@@ -593,6 +601,9 @@ static omerf_status brick_table_impl(const float aabb[6], const int32_t grid_res
   if (total > (1l << 31)) { set_error("too many bricks"); return OMERF_ESHAPE; }
   cudaStream_t s = (cudaStream_t)stream;
   if (fault_injected("launch")) return injected_launch_failure(entry);
+  omerf_status st = check_device_ptrs({{occ, "occ"}, {table, "table"}, {n_alloc, "n_alloc"},
+                                       {old_table, "old_table"}, {missing, "missing"}});
+  if (st != OMERF_OK) return st;
   if (missing) {
     cudaError_t e = cudaMemsetAsync(missing, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "brick table memset");
@@ -634,6 +645,7 @@ omerf_status omerf_ray_interval(const omerf_scene* s, const omerf_camera* cam, c
   }
   if (n == 0) return OMERF_OK;
   OMERF_LAUNCH_FAULT();
+  if ((st = check_device_ptrs({{cam ? nullptr : rays, "rays"}, {k_range, "k_range"}})) != OMERF_OK) return st;
   interval_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(s->geo, k, cam ? 1 : 0, rays, n,
                                                                                   reinterpret_cast<int2*>(k_range));
   cudaError_t e = cudaGetLastError();
@@ -663,6 +675,7 @@ omerf_status omerf_render(const omerf_scene* s, const omerf_camera* cam, const f
   }
   if (n == 0) return OMERF_OK;
   OMERF_LAUNCH_FAULT();
+  if ((st = check_device_ptr(cam ? nullptr : rays, "rays")) != OMERF_OK) return st;
   cudaError_t e = launch_march_fwd(s, cam ? &k : nullptr, rays, n, rgb, count, nullptr, nullptr, 0, nullptr,
                                    nullptr, nullptr, (cudaStream_t)stream);
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "render launch");
@@ -724,6 +737,17 @@ static omerf_status check_train_args(const omerf_scene* s, const float* rays, co
   return OMERF_OK;
 }
 
+// The arrays of a training call, checked to be device memory.
+static omerf_status check_train_ptrs(const float* rays, const float* target, const float* dirs, const void* saved,
+                                     const float* loss, const float* grad_scale, std::initializer_list<const float*> g) {
+  omerf_status st = check_device_ptrs({{rays, "rays"}, {target, "target"}, {dirs, "smooth_dirs"}, {saved, "saved"},
+                                       {loss, "loss"}, {grad_scale, "grad_scale"}});
+  if (st != OMERF_OK) return st;
+  for (const float* p : g)
+    if ((st = check_device_ptr(p, "gradient buffer")) != OMERF_OK) return st;
+  return OMERF_OK;
+}
+
 omerf_status omerf_train_fwd(const omerf_scene* s, const float* rays, const float* target, const float* smooth_dirs,
                              int64_t n, int32_t K, const float lambda[3], void* saved, float* loss, void* stream) {
   OMERF_API_RANGE();
@@ -731,6 +755,7 @@ omerf_status omerf_train_fwd(const omerf_scene* s, const float* rays, const floa
   if (st != OMERF_OK) return st;
   if (!loss) { set_error("loss is NULL"); return OMERF_EINVAL; }
   OMERF_LAUNCH_FAULT();
+  if ((st = check_train_ptrs(rays, target, smooth_dirs, saved, loss, nullptr, {})) != OMERF_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(loss, 0, 4 * sizeof(float), cs);
   if (e != cudaSuccess) return cuda_fail(e, "loss memset");
@@ -758,6 +783,9 @@ omerf_status omerf_train_bwd(const omerf_scene* s, const float* rays, const floa
     if (p && !aligned(p, 16)) { set_error("gradient buffers must be 16-byte aligned"); return OMERF_EINVAL; }
   if (g_occ && !aligned(g_occ, 8)) { set_error("g_occ must be 8-byte aligned"); return OMERF_EINVAL; }
   OMERF_LAUNCH_FAULT();
+  if ((st = check_train_ptrs(rays, target, smooth_dirs, saved, nullptr, grad_scale,
+                             {g_grid, g_xy, g_xz, g_yz, g_occ, g_mlp})) != OMERF_OK)
+    return st;
   cudaStream_t cs = (cudaStream_t)stream;
   cudaError_t e;
   if (n > 0) {
@@ -791,6 +819,9 @@ omerf_status omerf_train_step(const omerf_scene* s, const float* rays, const flo
     if (p && !aligned(p, 16)) { set_error("gradient buffers must be 16-byte aligned"); return OMERF_EINVAL; }
   if (g_occ && !aligned(g_occ, 8)) { set_error("g_occ must be 8-byte aligned"); return OMERF_EINVAL; }
   OMERF_LAUNCH_FAULT();
+  if ((st = check_train_ptrs(rays, target, smooth_dirs, saved, loss, nullptr,
+                             {g_grid, g_xy, g_xz, g_yz, g_occ, g_mlp})) != OMERF_OK)
+    return st;
   cudaStream_t cs = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(loss, 0, 4 * sizeof(float), cs);
   if (e != cudaSuccess) return cuda_fail(e, "loss memset");

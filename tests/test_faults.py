@@ -9,7 +9,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 LIB = os.path.join(ROOT, "paper_2404_09531_gb300", "libomerf.so")
-ECUDA = -4
+EDEVICE, ECUDA = -3, -4
 FAKE = ctypes.c_void_p(1 << 20)  # 1 MiB: aligned for every argument, never read
 
 
@@ -93,10 +93,12 @@ def _no_cuda_device():
 
 @pytest.mark.skipif(not _no_cuda_device(), reason="would launch a kernel on fake pointers")
 def test_unnamed_sites_do_not_fire(lib, fault):
-    """Only the named sites fire: with near-miss names the call goes on to its
-    launch, which fails for want of a device (this runs only where there is
-    no CUDA device), with the runtime's message instead of the injected one."""
+    """Only the named sites fire: with near-miss names the call goes on past
+    the launch hook to the device-memory check of its arrays, which fails for
+    want of a device (this runs only where there is no CUDA device), with
+    that check's message instead of the injected one."""
     fault("launchx,xlaunch,alloc")
     rc = lib.omerf_build_brick_table(_f32(-1, 1, -1, 1, -0.1, 0.1), _i32(16, 16, 8), 4, FAKE, 4, FAKE, FAKE, None)
-    assert rc == ECUDA
-    assert "fault injected" not in lib.omerf_last_error().decode()
+    assert rc == EDEVICE
+    msg = lib.omerf_last_error().decode()
+    assert "fault injected" not in msg and "occ" in msg

@@ -85,3 +85,43 @@ def test_injected_launch_failure(monkeypatch):
     rgb = om.render(scene, camera=cam)[0]
     torch.cuda.synchronize()
     np.testing.assert_array_equal(rgb.cpu().numpy(), ref.cpu().numpy())
+
+
+def test_host_arrays_rejected_before_any_launch():
+    """A pageable host array handed to an entry point as device data is
+    refused on the host (OMERF_EDEVICE, naming the argument) before anything
+    is launched, and the scene keeps working."""
+    import ctypes
+    scene = gpu_scene(synth.make_scene(1))
+    L = om.lib()
+    n = 64
+    rays_h = np.zeros((n, 6), np.float32)
+    rays_h[:, 2], rays_h[:, 5] = 1.0, -1.0
+    rays_d = torch.as_tensor(rays_h).cuda()
+    target = torch.zeros((n, 3), device="cuda")
+    saved = torch.empty(n * om.saved_bytes_per_ray() // 4, device="cuda")
+    loss = torch.zeros(4, device="cuda")
+    grads = om.zero_grads(scene)
+    g_host = np.zeros(scene.grid.numel(), np.float32)
+    lam = (ctypes.c_float * 3)(1.0, 0.0, 0.0)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    H = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    gp = [P(grads[k]) for k in ("grid", "p_xy", "p_xz", "p_yz", "occ", "mlp")]
+
+    rc = L.omerf_train_step(scene.handle, H(rays_h), P(target), None, n, 0, lam, P(saved), P(loss), *gp, None)
+    assert rc == -3 and "rays" in L.omerf_last_error().decode()
+    rc = L.omerf_train_step(scene.handle, P(rays_d), P(target), None, n, 0, lam, P(saved), P(loss), H(g_host),
+                            *gp[1:], None)
+    assert rc == -3 and "gradient" in L.omerf_last_error().decode()
+    rgb = torch.empty((n, 3), device="cuda")
+    rc = L.omerf_render(scene.handle, None, H(rays_h), n, P(rgb), None, None)
+    assert rc == -3 and "rays" in L.omerf_last_error().decode()
+    rc = L.omerf_sparsity_loss(scene.handle, H(rays_h[:, :3].copy()), n, ctypes.c_float(1.0), None, P(loss),
+                               *gp[:4], None)
+    assert rc == -3
+    assert not np.any(g_host)
+    # nothing was launched on the bad calls; the device arrays still work
+    rgb2, cnt = om.render(scene, rays=rays_d)
+    torch.cuda.synchronize()
+    assert torch.isfinite(rgb2).all() and cnt.shape == (n,)
+    om.sync()  # no error is pending from the refused calls
