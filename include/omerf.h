@@ -215,8 +215,9 @@ omerf_status omerf_render(const omerf_scene *scene, const omerf_camera *cam, con
  *     The address is kept for the life of the process: do not call this
  *     entry point on a device after cudaDeviceReset on it.
  *   - Pointers are checked as omerf_scene_create and omerf_render check them:
- *     the description's arrays must be device memory (OMERF_EDEVICE
- *     otherwise), rgb and count device or page-locked host memory.
+ *     the description's arrays and a ray list must be device memory
+ *     (OMERF_EDEVICE otherwise), rgb and count device or page-locked host
+ *     memory.
  *   - Scenes whose scratch does not fit are rejected with OMERF_ESHAPE: the
  *     coarse occupancy grid takes 8 bytes per cell (ceil(M / 2^l)^2 cells, l
  *     the smallest level whose cells span a 32-sample lattice window,

@@ -76,13 +76,15 @@ extern "C" omerf_status omerf_render_noalloc(const omerf_scene_desc* desc, const
     return OMERF_EINVAL;
   }
   // The same pointer checks as omerf_scene_create and omerf_render (none of
-  // them allocates): the description's arrays must be device memory, and the
-  // outputs device or page-locked host memory, written through its device alias.
+  // them allocates): the description's arrays and a ray list must be device
+  // memory, the outputs device or page-locked host memory, written through its
+  // device alias.
   const void* ptrs[] = {desc->grid, desc->brick_table, desc->plane_xy, desc->plane_xz, desc->plane_yz, desc->occ,
                         desc->mlp};
   const char* names[] = {"grid", "brick_table", "plane_xy", "plane_xz", "plane_yz", "occ", "mlp"};
   for (int i = 0; i < 7; i++)
     if ((st = check_device_ptr(ptrs[i], names[i])) != OMERF_OK) return st;
+  if (n > 0 && !cam && (st = check_device_ptr(rays, "rays")) != OMERF_OK) return st;
   if (n > 0) {
     void *rd = nullptr, *cd = nullptr;
     if ((st = output_ptr(rgb, &rd, "rgb")) != OMERF_OK) return st;

@@ -111,3 +111,18 @@ def test_output_pointers_are_checked_like_the_regular_render():
         assert rc == 0
         torch.cuda.synchronize()
         _check_same(ref, (pinned.cuda(), pinned_cnt.cuda()), f"page-locked output, call {call}")
+
+
+def test_host_ray_list_is_refused():
+    """A ray list in pageable host memory is refused with OMERF_EDEVICE."""
+    sc = synth.make_scene(1)
+    scene = gpu_scene(sc)
+    n = 64
+    rays = np.zeros((n, 6), np.float32)
+    rays[:, 5] = -1.0
+    rgb = torch.zeros((n, 3), device="cuda")
+    lib = om.lib()
+    rc = lib.omerf_render_noalloc(ctypes.byref(scene._desc), None, ctypes.c_void_p(rays.ctypes.data), n,
+                                  ctypes.c_void_p(rgb.data_ptr()), None, None)
+    assert rc == -3
+    assert b"rays" in lib.omerf_last_error()
