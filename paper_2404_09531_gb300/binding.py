@@ -421,8 +421,13 @@ def _train_inputs(scene, rays, target, smooth_dirs):
         dirs_t, K = None, 0
     else:
         dirs_t = _dev_f32(smooth_dirs, dev)
-        dirs_t = dirs_t.reshape(n, -1, 3)
-        K = int(dirs_t.shape[1])
+        if n == 0:
+            # an empty batch: K from a [0][K][3] array (nothing is read)
+            K = int(dirs_t.shape[1]) if dirs_t.dim() == 3 else 0
+            dirs_t = dirs_t.reshape(0, K, 3)
+        else:
+            dirs_t = dirs_t.reshape(n, -1, 3)
+            K = int(dirs_t.shape[1])
     return rays_t, target_t, dirs_t, n, K
 
 

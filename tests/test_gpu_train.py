@@ -266,3 +266,34 @@ def test_city_scene_training(dtype):
     assert np.count_nonzero(ref["grads"]["grid"]) > 10000
     np.testing.assert_allclose(float(res["loss"][0]), ref["loss"], rtol=1e-5)
     _check_grads(res, ref, what=f"city {dtype}")
+
+
+@pytest.mark.parametrize("n", [1, 31, 33])
+def test_ragged_small_batches(n):
+    """Batches that fill part of one or two 32-ray bundles."""
+    sc = synth.make_scene(3)
+    batch = synth.make_train_batch(3, n, seed=5 + n)
+    scene, res, ref = _run(sc, batch)
+    np.testing.assert_allclose(float(res["loss"][0]), ref["loss"], rtol=1e-5)
+    _check_grads(res, ref, what=f"n={n}")
+
+
+def test_zero_rays_leave_only_the_interval_span_term():
+    """An empty batch: the loss and gradients are those of the span term
+    lambda_7 sum (z_max - z_min)^2 alone (Eq. 5), the oracle's with the ray
+    terms switched off."""
+    sc = synth.make_scene(3)
+    scene = gpu_scene(sc)
+    empty = {k: v[:0] for k, v in synth.make_train_batch(3, 1, seed=2).items()}
+    res = om.train_step(scene, empty["rays"], empty["target"], empty["smooth_dirs"], lam=LAM)
+    torch.cuda.synchronize()
+    one = synth.make_train_batch(3, 1, seed=2)
+    ref = oracle.train(oracle.OracleScene(sc), one["rays"], one["target"], one["smooth_dirs"], lam=(0.0, 0.0, LAM[2]))
+    np.testing.assert_allclose(float(res["loss"][0]), ref["loss"], rtol=1e-5)
+    for k in KEYS:
+        g = res["grads"][k].cpu().numpy()
+        if k == "occ":
+            nrel, mrel = grad_errors(g, ref["grads"][k])
+            assert nrel <= GRAD_RTOL and mrel <= GRAD_RTOL, f"occ: {nrel:.2e} {mrel:.2e}"
+        else:
+            assert not np.any(g), k
