@@ -72,3 +72,41 @@ def test_two_processes_match_the_full_batch_and_the_oracle():
         assert np.linalg.norm(g - f) <= 1e-5 * np.linalg.norm(f) + 1e-12, k
         nrel, mrel = grad_errors(got[k], ref["grads"][k])
         assert nrel <= GRAD_RTOL and mrel <= GRAD_RTOL, (k, nrel, mrel)
+
+
+def _worker_small(rank, world, init, out, n):
+    import torch.distributed as dist
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", init_method=init, rank=rank, world_size=world)
+    sc = synth.make_scene(3)
+    b = synth.make_train_batch(3, max(n, 1), seed=9)
+    scene = om.scene_from_synth(sc, device="cuda")
+    shapes = {k: tuple(getattr(scene, k).shape) for k in dp.GRAD_KEYS}
+    step = dp.DataParallelStep(shapes, torch.device("cuda"))
+    rays, tgt, dirs = (torch.as_tensor(b[k][:n]).cuda() for k in ("rays", "target", "smooth_dirs"))
+    step(scene, rays, tgt, dirs, LAM)
+    torch.cuda.synchronize()
+    if rank == 0:
+        np.savez(out, loss=step.loss.cpu().numpy(), **{k: v.cpu().numpy() for k, v in step.grads.items()})
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("n", [0, 1])
+def test_batches_smaller_than_the_world(n):
+    """One ray (rank 1's shard is empty) and no ray at all (rank 0 still adds
+    the interval-span term): equal to the single-process step."""
+    import torch.multiprocessing as mp
+    with tempfile.TemporaryDirectory() as tmp:
+        out = os.path.join(tmp, "rank0.npz")
+        mp.start_processes(_worker_small, args=(2, "file://" + os.path.join(tmp, "store"), out, n), nprocs=2,
+                           join=True, start_method="spawn")
+        got = np.load(out)
+    sc = synth.make_scene(3)
+    b = synth.make_train_batch(3, max(n, 1), seed=9)
+    scene = om.scene_from_synth(sc, device="cuda")
+    full = om.train_step(scene, b["rays"][:n], b["target"][:n], b["smooth_dirs"][:n], lam=LAM)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(got["loss"], full["loss"].cpu().numpy(), rtol=1e-6, atol=1e-12)
+    for k in dp.GRAD_KEYS:
+        np.testing.assert_allclose(got[k], full["grads"][k].cpu().numpy(), rtol=1e-6, atol=1e-12, err_msg=k)
