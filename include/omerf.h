@@ -126,8 +126,11 @@ typedef struct omerf_scene omerf_scene;
  * the grid (nbx * nby * nbz, stored or not).  It builds
  * that state on `stream`; for a brick grid it then waits for the stream and
  * checks that every table entry is -1 or a valid pool index (OMERF_ESHAPE
- * otherwise).  Errors: OMERF_EINVAL / OMERF_ESHAPE for bad descriptions,
- * OMERF_ENOMEM / OMERF_ECUDA if its state cannot be allocated. */
+ * otherwise).  Texels are addressed with 32-bit element offsets, so the
+ * dense grid (or the brick pool) and each plane must hold fewer than 2^31
+ * elements (OMERF_ESHAPE otherwise).  Errors: OMERF_EINVAL / OMERF_ESHAPE
+ * for bad descriptions, OMERF_ENOMEM / OMERF_ECUDA if its state cannot be
+ * allocated. */
 omerf_status omerf_scene_create(const omerf_scene_desc *desc, void *stream, omerf_scene **out);
 
 /* Recompute the scene's occupancy hull after the caller changed occ in

@@ -47,7 +47,7 @@ struct Geo {
   const float2* occ;
   const float* mlp;
   const float* hull;       // device [2]: min z_min, max z_max over non-empty cells
-  const int* nbr;          // device [nbx * nby * nbz][8]: pool index of the (+dx, +dy, +dz) neighbours
+  const int* nbr;          // device [nbx * nby * nbz][8]: pool element offset of the (+dx, +dy, +dz) neighbours
   const float2* chull;     // device [Mc][Mc]: coarse max-pooled (min z_min, max z_max)
   int clog2;               // coarse cell = 2^clog2 x 2^clog2 occupancy cells
   int Mc;                  // coarse cells per axis
@@ -336,10 +336,11 @@ __device__ __forceinline__ void grid_stencil(const Geo& g, const float p[3], int
   } else {
     // brick grid: a cell inside its brick reads all corners from the brick's
     // table entry; a cell reaching into neighbour bricks reads the record of
-    // its lowest corner's brick (one 256-bit load: the pool index of the
-    // brick of every corner, stored or not), so every corner is read through
-    // its own brick without branching on which ones are stored
-    const int s = g.blog2, m = (1 << s) - 1, B = 1 << s;
+    // its lowest corner's brick (one 256-bit load: the pool element offset
+    // of the brick of every corner, stored or not), so every corner is read
+    // through its own brick without branching on which ones are stored.  A
+    // corner's offset is its brick's offset plus per-axis local offsets.
+    const int s = g.blog2, m = (1 << s) - 1;
     const int lin = ((i[0] >> s) * g.nb[1] + (i[1] >> s)) * g.nb[2] + (i[2] >> s);
     const int cx = (i[0] & m) == m, cy = (i[1] & m) == m, cz = (i[2] & m) == m;
     int nb[8];
@@ -350,9 +351,13 @@ __device__ __forceinline__ void grid_stencil(const Geo& g, const float p[3], int
                    : "l"(g.nbr + 8 * lin));
     } else {
       const int b0 = __ldg(g.table + lin);
+      const int o0 = b0 < 0 ? -1 : (b0 << (3 * s + 3));
 #pragma unroll
-      for (int c = 0; c < 8; c++) nb[c] = b0;
+      for (int c = 0; c < 8; c++) nb[c] = o0;
     }
+    const int lx[2] = {(i[0] & m) << (2 * s + 3), ((i[0] + 1) & m) << (2 * s + 3)};
+    const int ly[2] = {(i[1] & m) << (s + 3), ((i[1] + 1) & m) << (s + 3)};
+    const int lz[2] = {(i[2] & m) << 3, ((i[2] + 1) & m) << 3};
 #pragma unroll
     for (int c = 0; c < 8; c++) {
       const int dx = (c >> 2) & 1, dy = (c >> 1) & 1, dz = c & 1;
@@ -361,8 +366,7 @@ __device__ __forceinline__ void grid_stencil(const Geo& g, const float p[3], int
       const int z0 = kz ? nb[1] : nb[0], z1 = kz ? nb[3] : nb[2], z2 = kz ? nb[5] : nb[4], z3 = kz ? nb[7] : nb[6];
       const int y0 = ky ? z1 : z0, y1 = ky ? z3 : z2;
       const int b = kx ? y1 : y0;
-      const int li = (i[0] + dx) & m, lj = (i[1] + dy) & m, lk = (i[2] + dz) & m;
-      off[c] = b < 0 ? -1 : ((((b * B + li) * B + lj) * B) + lk) * kNch;
+      off[c] = b < 0 ? -1 : b + lx[dx] + ly[dy] + lz[dz];
     }
     check_unallocated(g, off);
   }

@@ -130,13 +130,14 @@ __global__ void brick_flag_kernel(const BrickArgs a, long total) {
 }
 
 // Neighbour records of a brick grid, one per brick of the grid (stored or
-// not): nbr[id][dx*4 + dy*2 + dz] is the pool index of the brick at
-// (bi + dx, bj + dy, bk + dz), -1 if it is not stored or outside the grid
-// (slot 0 is the brick's own table entry).  A sample whose cell reaches
+// not): nbr[id][dx*4 + dy*2 + dz] is the element offset in the pool
+// (pool index << shift, shift = log2 of a brick's B^3 x 8 elements) of the
+// brick at (bi + dx, bj + dy, bk + dz), -1 if it is not stored or outside
+// the grid (slot 0 is the brick's own table entry).  A sample whose cell reaches
 // into neighbour bricks finds the brick of each of its 8 corners in the
 // record of its lowest corner's brick, with one 256-bit load.
 __global__ void brick_neighbor_kernel(const int* __restrict__ table, int nbx, int nby, int nbz, int n_bricks,
-                                      int* __restrict__ nbr) {
+                                      int shift, int* __restrict__ nbr) {
   const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (long)nbx * nby * nbz) return;
   const int bk = (int)(id % nbz), bj = (int)((id / nbz) % nby), bi = (int)(id / ((long)nbz * nby));
@@ -146,7 +147,7 @@ __global__ void brick_neighbor_kernel(const int* __restrict__ table, int nbx, in
     const int x = bi + ((c >> 2) & 1), y = bj + ((c >> 1) & 1), z = bk + (c & 1);
     int b = -1;
     if (x < nbx && y < nby && z < nbz) b = table[((long)x * nby + y) * nbz + z];
-    v[c] = (b >= 0 && b < n_bricks) ? b : -1;
+    v[c] = (b >= 0 && b < n_bricks) ? (b << shift) : -1;
   }
   int4* out = reinterpret_cast<int4*>(nbr + 8l * id);
   out[0] = make_int4(v[0], v[1], v[2], v[3]);
@@ -289,6 +290,19 @@ omerf_status validate_desc(const omerf_scene_desc* d) {
     if (!d->brick_table) { set_error("brick_table is NULL for a brick grid"); return OMERF_EINVAL; }
     if (d->n_bricks < 0) { set_error("n_bricks must be >= 0"); return OMERF_ESHAPE; }
   }
+  // the kernels address texels with 32-bit element offsets
+  const long long B3 = d->brick ? (long long)d->brick * d->brick * d->brick : 0;
+  const long long grid_elems =
+      (d->brick ? (long long)d->n_bricks * B3 : (long long)d->grid_res[0] * d->grid_res[1] * d->grid_res[2]) * kNch;
+  const long long plane_elems[3] = {(long long)d->plane_res[0] * d->plane_res[1] * kNch,
+                                    (long long)d->plane_res[0] * d->plane_res[2] * kNch,
+                                    (long long)d->plane_res[1] * d->plane_res[2] * kNch};
+  if (grid_elems > 0x7fffffffLL || plane_elems[0] > 0x7fffffffLL || plane_elems[1] > 0x7fffffffLL ||
+      plane_elems[2] > 0x7fffffffLL) {
+    set_error("a feature array holds 2^31 or more elements (grid or pool %lld, planes %lld / %lld / %lld)",
+              grid_elems, plane_elems[0], plane_elems[1], plane_elems[2]);
+    return OMERF_ESHAPE;
+  }
   if (!d->grid || !d->plane_xy || !d->plane_xz || !d->plane_yz || !d->occ || !d->mlp) {
     set_error("a scene array pointer is NULL");
     return OMERF_EINVAL;
@@ -391,7 +405,8 @@ omerf_status build_brick_neighbors(omerf_scene* s, cudaStream_t stream) {
   const long total = (long)g.nb[0] * g.nb[1] * g.nb[2];
   if (total > 0)
     brick_neighbor_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(s->desc.brick_table, g.nb[0], g.nb[1],
-                                                                              g.nb[2], s->desc.n_bricks, s->nbr);
+                                                                              g.nb[2], s->desc.n_bricks,
+                                                                              3 * g.blog2 + 3, s->nbr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? OMERF_OK : cuda_fail(e, "neighbour record kernel");
 }

@@ -70,6 +70,20 @@ def test_host_validation_without_gpu(lib):
     assert lib.omerf_scene_create(ctypes.byref(d), None, ctypes.byref(out)) == -1
     assert b"aligned" in lib.omerf_last_error()
     assert lib.omerf_scene_create(None, None, ctypes.byref(out)) == -1
+    # texels are addressed with 32-bit element offsets: arrays of 2^31 or more
+    # elements are refused (dense grid, brick pool, each plane)
+    d.grid = 4096
+    d.grid_res[:] = [2048, 2048, 64]  # 2^31 elements
+    assert lib.omerf_scene_create(ctypes.byref(d), None, ctypes.byref(out)) == -2
+    assert b"2^31" in lib.omerf_last_error()
+    d.grid_res[:] = [2048, 2048, 63]
+    d.plane_res[:] = [16384, 16384, 4]  # XY plane 2^31 elements
+    assert lib.omerf_scene_create(ctypes.byref(d), None, ctypes.byref(out)) == -2
+    d.plane_res[:] = [4, 4, 4]
+    d.brick, d.brick_table, d.n_bricks = 8, 4096, 1 << 19  # pool of 2^19 bricks of 8^3 x 8 = 2^31 elements
+    assert lib.omerf_scene_create(ctypes.byref(d), None, ctypes.byref(out)) == -2
+    d.brick, d.brick_table, d.n_bricks = 0, None, 0
+    d.grid_res[:] = [4, 4, 4]
     aabb = (ctypes.c_float * 6)(-1, 1, -1, 1, -1, 1)
     res = (ctypes.c_int32 * 3)(8, 8, 8)
     assert lib.omerf_build_brick_table(aabb, res, 3, ctypes.c_void_p(4096), 4, ctypes.c_void_p(4096),
