@@ -315,7 +315,7 @@ __device__ __forceinline__ bool in_range(const Geo& g, int q, int off) {
 #endif
 }
 
-// Element offsets of the 8 grid corners (-1 for an unallocated brick) and
+// Element offsets of the 8 grid corners (negative for an unallocated brick) and
 // their trilinear weights, corner order (dx, dy, dz) with dz fastest.
 template <bool SPARSE>
 __device__ __forceinline__ void grid_stencil(const Geo& g, const float p[3], int off[8], float w[8]) {
@@ -350,8 +350,9 @@ __device__ __forceinline__ void grid_stencil(const Geo& g, const float p[3], int
                      "=r"(nb[7])
                    : "l"(g.nbr + 8 * lin));
     } else {
-      const int b0 = __ldg(g.table + lin);
-      const int o0 = b0 < 0 ? -1 : (b0 << (3 * s + 3));
+      // a table entry of -1 (not stored) shifts to -2^(3s+3), below minus
+      // any local offset, so the corner offsets through it stay negative
+      const int o0 = __ldg(g.table + lin) << (3 * s + 3);
 #pragma unroll
       for (int c = 0; c < 8; c++) nb[c] = o0;
     }
@@ -366,7 +367,7 @@ __device__ __forceinline__ void grid_stencil(const Geo& g, const float p[3], int
       const int z0 = kz ? nb[1] : nb[0], z1 = kz ? nb[3] : nb[2], z2 = kz ? nb[5] : nb[4], z3 = kz ? nb[7] : nb[6];
       const int y0 = ky ? z1 : z0, y1 = ky ? z3 : z2;
       const int b = kx ? y1 : y0;
-      off[c] = b < 0 ? -1 : b + lx[dx] + ly[dy] + lz[dz];
+      off[c] = b + lx[dx] + ly[dy] + lz[dz];  // negative through an unstored brick
     }
     check_unallocated(g, off);
   }

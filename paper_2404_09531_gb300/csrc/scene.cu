@@ -132,8 +132,9 @@ __global__ void brick_flag_kernel(const BrickArgs a, long total) {
 // Neighbour records of a brick grid, one per brick of the grid (stored or
 // not): nbr[id][dx*4 + dy*2 + dz] is the element offset in the pool
 // (pool index << shift, shift = log2 of a brick's B^3 x 8 elements) of the
-// brick at (bi + dx, bj + dy, bk + dz), -1 if it is not stored or outside
-// the grid (slot 0 is the brick's own table entry).  A sample whose cell reaches
+// brick at (bi + dx, bj + dy, bk + dz), -2^shift if it is not stored or
+// outside the grid, so that the brick offset plus any local offset (less
+// than 2^shift) stays negative (slot 0 is the brick's own table entry).  A sample whose cell reaches
 // into neighbour bricks finds the brick of each of its 8 corners in the
 // record of its lowest corner's brick, with one 256-bit load.
 __global__ void brick_neighbor_kernel(const int* __restrict__ table, int nbx, int nby, int nbz, int n_bricks,
@@ -147,7 +148,7 @@ __global__ void brick_neighbor_kernel(const int* __restrict__ table, int nbx, in
     const int x = bi + ((c >> 2) & 1), y = bj + ((c >> 1) & 1), z = bk + (c & 1);
     int b = -1;
     if (x < nbx && y < nby && z < nbz) b = table[((long)x * nby + y) * nbz + z];
-    v[c] = (b >= 0 && b < n_bricks) ? (b << shift) : -1;
+    v[c] = ((b >= 0 && b < n_bricks) ? b : -1) << shift;
   }
   int4* out = reinterpret_cast<int4*>(nbr + 8l * id);
   out[0] = make_int4(v[0], v[1], v[2], v[3]);
