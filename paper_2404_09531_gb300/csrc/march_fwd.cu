@@ -300,10 +300,34 @@ __global__ void __launch_bounds__(kThreads, OMERF_FWD_MINB) march_fwd_kernel(con
   }
 }
 
+#ifndef OMERF_CARVEOUT
+#define OMERF_CARVEOUT 1
+#endif
 int persistent_blocks(const void* kernel, int threads, size_t smem, int num_sms) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
+#if OMERF_CARVEOUT
+  // The marches' gathers are served from L1, which shares each SM's SRAM
+  // with shared memory: ask for the smallest shared-memory carveout that
+  // still holds per_sm blocks (with the driver's 1 KB per block), leaving
+  // the rest to L1; keep it only if the occupancy still holds.
+  cudaFuncAttributes fa;
+  int dev = 0, max_smem = 0;
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+      max_smem > 0) {
+    const size_t need = (fa.sharedSizeBytes + smem + 1024) * (size_t)per_sm;
+    const int pct = (int)((need * 100 + (size_t)max_smem - 1) / (size_t)max_smem);
+    if (pct < 100 && cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct) == cudaSuccess) {
+      int again = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&again, kernel, threads, smem) != cudaSuccess ||
+          again < per_sm)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutDefault);
+    }
+  }
+  cudaGetLastError();  // a refused hint is not an error of the launch
+#endif
   return per_sm * num_sms;
 }
 
