@@ -813,7 +813,7 @@ def run_native(args):
                              "traffic_frac": (traffic_per_launch() / t_launch / 1e9 / hbm)
                              if traffic_per_launch() else None},
                      "probes": peaks,
-                     "note": "the gather is served from L1 (85-88 % hits) and L2 (97 %): the algorithmic bytes "
+                     "note": "the gather is served from L1 (92 % hits) and L2 (94-97 %): the algorithmic bytes "
                              "are bytes delivered to registers, bounded by L1's load bandwidth; DRAM moves only "
                              "each frame's working set (traffic: null when the kernel's sources differ from "
                              "those of the recorded ncu capture)"},
