@@ -26,21 +26,28 @@
 
 namespace omerf {
 
-// Per-warp shared state of the packed march of one bundle of 32 rays.  With
-// the tensor-core MLP the sample queue doubles as the MLP staging area.
-struct QueueOnly {
+// Per-warp shared state of the packed march of one bundle of 32 rays.
+struct MarchState {
   WarpQueue q;
-};
-union QueueOrStage {
-  WarpQueue q;
-  MlpStage m;
-};
-template <bool MMA>
-struct WarpMarch {
-  typename std::conditional<MMA, QueueOrStage, QueueOnly>::type u;
   float F[32][8];    // per-ray accumulated [sum w c^d, sum w f]
   float T[32];       // per-ray transmittance so far
   int cnt[32];       // per-ray evaluated samples
+};
+// With the tensor-core MLP the whole march state doubles as the MLP staging
+// area: the epilogue copies each ray's F, T and count to registers before it
+// stages the MLP rows, and the next bundle starts after a CTA barrier.  The
+// smaller per-warp footprint lets the BF16 render take a smaller
+// shared-memory carveout, leaving more of the SM's SRAM to L1.
+template <bool MMA>
+struct WarpMarch {
+  MarchState s;
+};
+template <>
+struct WarpMarch<true> {
+  union {
+    MarchState s;
+    MlpStage m;
+  };
 };
 
 // March the 32 rays of a bundle (lane r owns ray r: o, d, [klo, khi]).
@@ -52,25 +59,25 @@ struct WarpMarch {
 //          1 - alpha_hat, early termination is resolved per segment, and
 //          the weighted features are summed per segment into the ray's
 //          accumulator.
-// On return ws.F / ws.T / ws.cnt hold every ray's F, T_N and sample count.
+// On return ws.s.F / ws.s.T / ws.s.cnt hold every ray's F, T_N and sample count.
 template <class FT, bool SPARSE, class WS>
 __device__ __forceinline__ void march_bundle(const Geo& g, int lane, const float o[3], const float d[3], int klo,
                                              int khi, bool any, WS& ws) {
 #pragma unroll
-  for (int c = 0; c < 8; c++) ws.F[lane][c] = 0.0f;
-  ws.T[lane] = 1.0f;
-  ws.cnt[lane] = 0;
-  ws.u.q.ro[lane] = make_float4(o[0], o[1], o[2], __int_as_float(klo));
-  ws.u.q.rd[lane] = make_float4(d[0], d[1], d[2], __int_as_float(khi));
-  ws.u.q.cap[lane] = g.n_max;
+  for (int c = 0; c < 8; c++) ws.s.F[lane][c] = 0.0f;
+  ws.s.T[lane] = 1.0f;
+  ws.s.cnt[lane] = 0;
+  ws.s.q.ro[lane] = make_float4(o[0], o[1], o[2], __int_as_float(klo));
+  ws.s.q.rd[lane] = make_float4(d[0], d[1], d[2], __int_as_float(khi));
+  ws.s.q.cap[lane] = g.n_max;
   unsigned pend = __ballot_sync(kFull, any);
   FillState f;
   __syncwarp();
   while (pend) {
-    const int nq = fill_queue(g, lane, pend, f, ws.u.q);
+    const int nq = fill_queue(g, lane, pend, f, ws.s.q);
     if (nq == 0) break;
     const bool act = lane < nq;
-    const float4 qa = ws.u.q.a[lane], qb = ws.u.q.b[lane];
+    const float4 qa = ws.s.q.a[lane], qb = ws.s.q.b[lane];
     const int r = act ? __float_as_int(qb.y) : 32;
     SampleAct s;
     s.ah = 0.0f;
@@ -88,7 +95,7 @@ __device__ __forceinline__ void march_bundle(const Geo& g, int lane, const float
     const float P = seg_prod_scan(1.0f - s.ah, lane, segstart);
     float Pex = __shfl_up_sync(kFull, P, 1);
     if (head) Pex = 1.0f;
-    const float Tprev = act ? ws.T[r] : 1.0f;
+    const float Tprev = act ? ws.s.T[r] : 1.0f;
     const float Ti = Tprev * Pex, Tn = Tprev * P;
     // early termination: the first sample of a segment whose T drops below t_thr ends the ray
     const bool term = act && Tn < g.t_thr;
@@ -107,12 +114,12 @@ __device__ __forceinline__ void march_bundle(const Geo& g, int lane, const float
     const unsigned segle = lanemask_le() & ~((1u << segstart) - 1u);
     if (tail) {
 #pragma unroll
-      for (int c = 0; c < 7; c++) ws.F[r][c] += wx[c];
-      ws.cnt[r] += __popc(okm & segle);
-      if (!(tm & segle)) ws.T[r] = Tn;
+      for (int c = 0; c < 7; c++) ws.s.F[r][c] += wx[c];
+      ws.s.cnt[r] += __popc(okm & segle);
+      if (!(tm & segle)) ws.s.T[r] = Tn;
     }
     const bool first_term = term && !dropped;
-    if (first_term) ws.T[r] = Tn;
+    if (first_term) ws.s.T[r] = Tn;
     pend &= ~__reduce_or_sync(kFull, first_term ? (1u << r) : 0u);
     __syncwarp();
   }
@@ -214,15 +221,15 @@ __global__ void __launch_bounds__(kThreads, OMERF_FWD_MINB) march_fwd_kernel(con
     march_bundle<FT, SPARSE>(g, lane, o, d, klo, khi, any, ws);
     float F[7];
 #pragma unroll
-    for (int c = 0; c < 7; c++) F[c] = ws.F[lane][c];
-    const float T = ws.T[lane];
-    const int cnt = ws.cnt[lane];
+    for (int c = 0; c < 7; c++) F[c] = ws.s.F[lane][c];
+    const float T = ws.s.T[lane];
+    const int cnt = ws.s.cnt[lane];
     __syncwarp();
 
     float yd_mma[3] = {0.0f, 0.0f, 0.0f};
     if constexpr (kMMA) {
-      mlp_stage_row(ws.u.m, lane, valid && cnt > 0, F, d);
-      mlp_bf16_warp(sFrag, ws.u.m, lane, yd_mma);
+      mlp_stage_row(ws.m, lane, valid && cnt > 0, F, d);
+      mlp_bf16_warp(sFrag, ws.m, lane, yd_mma);
     }
     if (valid && (!TRAIN || LOSS)) {
       float out[3], yd[3] = {0.0f, 0.0f, 0.0f};
