@@ -133,6 +133,13 @@ typedef struct omerf_scene omerf_scene;
  * allocated. */
 omerf_status omerf_scene_create(const omerf_scene_desc *desc, void *stream, omerf_scene **out);
 
+/* Device memory in bytes that omerf_scene_create allocates for this
+ * description (the handle's own state listed above; the caller's arrays are
+ * not counted), or the negative status omerf_scene_create would return
+ * for an invalid description (the same host checks; no pointer is read or
+ * queried).  Host only: no CUDA call, no allocation. */
+int64_t omerf_scene_device_bytes(const omerf_scene_desc *desc);
+
 /* Recompute the scene's occupancy hull after the caller changed occ in
  * place (for example after an optimiser step on z_min / z_max). */
 omerf_status omerf_scene_update(omerf_scene *scene, void *stream);

@@ -26,6 +26,7 @@ from .binding import (  # noqa: F401
     plane_crop_rows,
     probe_load_bandwidth,
     probe_red_bandwidth,
+    scene_device_bytes,
     ray_interval,
     render,
     render_cameras,
@@ -44,6 +45,6 @@ from .binding import (  # noqa: F401
 __all__ = [
     "OmerfError", "Scene", "TrainStep", "Trainer", "adam_step", "build_brick_table", "camera_struct", "check_counts", "check_totals",
     "crop_planes", "entropy_loss", "extract_bricks", "grow_brick_table", "lambda_occ", "lib", "lr_exponential", "occupancy_grid",
-    "plane_crop_rows", "probe_load_bandwidth", "probe_red_bandwidth", "ray_interval", "render", "render_cameras", "render_noalloc", "saved_bytes_per_ray", "scene_from_synth",
+    "plane_crop_rows", "probe_load_bandwidth", "probe_red_bandwidth", "scene_device_bytes", "ray_interval", "render", "render_cameras", "render_noalloc", "saved_bytes_per_ray", "scene_from_synth",
     "sparsity_loss", "sync", "train_bwd", "train_fwd", "train_step", "unpack_occupancy_bits", "zero_grads",
 ]

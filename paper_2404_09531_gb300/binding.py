@@ -89,6 +89,7 @@ SIGNATURES = {
     "omerf_lambda_occ": (ctypes.c_float, [_L]),
     "omerf_probe_load_bandwidth": (ctypes.c_int, [_P, _L, _I, _I, _P, _P]),
     "omerf_probe_red_bandwidth": (ctypes.c_int, [_P, _L, _I, _I, _P]),
+    "omerf_scene_device_bytes": (ctypes.c_int64, [_P]),
     "omerf_check_build": (ctypes.c_int32, []),
     "omerf_check_counts": (ctypes.c_int, [_P, _P, _I, _P]),
     "omerf_check_totals": (None, [_P]),
@@ -658,6 +659,15 @@ def probe_load_bandwidth(buf: torch.Tensor, bytes_per_cta: int, ctas: int, passe
     _check(lib().omerf_probe_load_bandwidth(_ptr(buf), int(bytes_per_cta), int(ctas), int(passes), _ptr(sink),
                                             _stream(stream)), "omerf_probe_load_bandwidth")
     return int(ctas) * int(bytes_per_cta) * int(passes)
+
+
+def scene_device_bytes(scene: Scene) -> int:
+    """Device bytes the scene handle allocates for its own state (the
+    caller's arrays not counted)."""
+    n = int(lib().omerf_scene_device_bytes(ctypes.byref(scene._desc)))
+    if n < 0:
+        raise OmerfError(f"omerf_scene_device_bytes: status {n}")
+    return n
 
 
 def probe_red_bandwidth(buf: torch.Tensor, bytes_per_warp: int, ctas: int, passes: int, stream=None):

@@ -424,6 +424,18 @@ void choose_coarse_level(omerf_scene* s) {
   s->Mc = (d.occ_res + (1 << l) - 1) >> l;
 }
 
+// Device bytes of a scene handle's own state, in the order omerf_scene_create
+// allocates it: hull state, work counters, coarse occupancy grid, camera
+// records, brick neighbour records, the checking build's counters.
+static void scene_alloc_bytes(const omerf_scene_desc* d, int Mc, size_t out[6]) {
+  out[0] = 64 * sizeof(float);
+  out[1] = kCounterSlots * sizeof(unsigned);
+  out[2] = (size_t)Mc * Mc * sizeof(float2);
+  out[3] = kMaxCams * sizeof(CamRec);
+  out[4] = d->brick ? brick_records_bytes(d) : 0;
+  out[5] = OMERF_CHECK ? 2 * sizeof(unsigned long long) : 0;
+}
+
 omerf_status validate_camera(const omerf_camera* c, int64_t n) {
   if (c->width < 1 || c->height < 1 || (int64_t)c->width * c->height != n) {
     set_error("camera size %d x %d does not match n = %lld", c->width, c->height, (long long)n);
@@ -500,17 +512,19 @@ omerf_status omerf_scene_create(const omerf_scene_desc* desc, void* stream, omer
   cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (s->num_sms < 1) s->num_sms = 1;
   // OMERF_FAULT=alloc: the handle's first allocation fails (tests of the path)
-  e = fault_injected("alloc") ? cudaErrorMemoryAllocation : cudaMalloc(&s->state, 64 * sizeof(float));
-  if (e != cudaSuccess) { cudaGetLastError(); delete s; set_error("cudaMalloc: %s", cudaGetErrorString(e)); return OMERF_ENOMEM; }
-  e = cudaMalloc(&s->counters, kCounterSlots * sizeof(unsigned));
-  if (e != cudaSuccess) { cudaGetLastError(); cudaFree(s->state); delete s; set_error("cudaMalloc: %s", cudaGetErrorString(e)); return OMERF_ENOMEM; }
   choose_coarse_level(s);
-  e = cudaMalloc(&s->chull, (size_t)s->Mc * s->Mc * sizeof(float2));
-  if (e == cudaSuccess) e = cudaMalloc(&s->cams, kMaxCams * sizeof(CamRec));
-  if (e == cudaSuccess && desc->brick) e = cudaMalloc(&s->nbr, brick_records_bytes(desc));
-  if (OMERF_CHECK && e == cudaSuccess) {
-    e = cudaMalloc(&s->check, 2 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(s->check, 0, 2 * sizeof(unsigned long long));
+  size_t bytes[6];
+  scene_alloc_bytes(desc, s->Mc, bytes);
+  e = fault_injected("alloc") ? cudaErrorMemoryAllocation : cudaMalloc(&s->state, bytes[0]);
+  if (e != cudaSuccess) { cudaGetLastError(); delete s; set_error("cudaMalloc: %s", cudaGetErrorString(e)); return OMERF_ENOMEM; }
+  e = cudaMalloc(&s->counters, bytes[1]);
+  if (e != cudaSuccess) { cudaGetLastError(); cudaFree(s->state); delete s; set_error("cudaMalloc: %s", cudaGetErrorString(e)); return OMERF_ENOMEM; }
+  e = cudaMalloc(&s->chull, bytes[2]);
+  if (e == cudaSuccess) e = cudaMalloc(&s->cams, bytes[3]);
+  if (e == cudaSuccess && bytes[4]) e = cudaMalloc(&s->nbr, bytes[4]);
+  if (e == cudaSuccess && bytes[5]) {
+    e = cudaMalloc(&s->check, bytes[5]);
+    if (e == cudaSuccess) e = cudaMemset(s->check, 0, bytes[5]);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -551,6 +565,19 @@ omerf_status omerf_scene_create(const omerf_scene_desc* desc, void* stream, omer
   if (st != OMERF_OK) { omerf_scene_destroy(s); return st; }
   *out = s;
   return OMERF_OK;
+}
+
+int64_t omerf_scene_device_bytes(const omerf_scene_desc* desc) {
+  const omerf_status st = validate_desc(desc);
+  if (st != OMERF_OK) return st;
+  omerf_scene s;
+  s.desc = *desc;
+  choose_coarse_level(&s);
+  size_t bytes[6];
+  scene_alloc_bytes(desc, s.Mc, bytes);
+  size_t total = 0;
+  for (size_t b : bytes) total += b;
+  return (int64_t)total;
 }
 
 omerf_status omerf_scene_update(omerf_scene* s, void* stream) {

@@ -70,6 +70,20 @@ def test_host_validation_without_gpu(lib):
     assert lib.omerf_scene_create(ctypes.byref(d), None, ctypes.byref(out)) == -1
     assert b"aligned" in lib.omerf_last_error()
     assert lib.omerf_scene_create(None, None, ctypes.byref(out)) == -1
+    # size query: host-only, the same validation; a brick grid adds one
+    # 32-byte neighbour record per brick of the grid
+    lib.omerf_scene_device_bytes.restype = ctypes.c_int64
+    d.grid = 4096
+    dense = lib.omerf_scene_device_bytes(ctypes.byref(d))
+    assert dense > 0
+    d.grid_res[:] = [16, 24, 8]
+    d.brick, d.brick_table, d.n_bricks = 4, 4096, 10
+    assert lib.omerf_scene_device_bytes(ctypes.byref(d)) - dense == 32 * (4 * 6 * 2)
+    d.brick, d.brick_table, d.n_bricks = 0, None, 0
+    d.grid_res[:] = [4, 4, 4]
+    d.step = 0.3
+    assert lib.omerf_scene_device_bytes(ctypes.byref(d)) == -1
+    d.step = 1 / 64
     # texels are addressed with 32-bit element offsets: arrays of 2^31 or more
     # elements are refused (dense grid, brick pool, each plane)
     d.grid = 4096
