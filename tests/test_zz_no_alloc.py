@@ -126,3 +126,23 @@ def test_host_ray_list_is_refused():
                                   ctypes.c_void_p(rgb.data_ptr()), None, None)
     assert rc == -3
     assert b"rays" in lib.omerf_last_error()
+
+
+def test_repeated_calls_leave_no_device_allocation_behind():
+    """After a first call (which loads the module and its static scratch),
+    50 more calls on preallocated outputs leave the device's free memory
+    unchanged: no call keeps an allocation.  (A cudaMalloc / cudaFree pair
+    within one call would not show here.)"""
+    sc = synth.make_scene(2)
+    scene = gpu_scene(sc)
+    cam = synth.make_cameras(2)[1]
+    n = cam["width"] * cam["height"]
+    rgb = torch.empty((n, 3), device="cuda")
+    cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+    om.render_noalloc(scene, camera=cam, rgb=rgb, count=cnt)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(50):
+        om.render_noalloc(scene, camera=cam, rgb=rgb, count=cnt)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
